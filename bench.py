@@ -1,0 +1,279 @@
+#!/usr/bin/env python3
+"""Benchmark: sem_ax GDOF/s and PCG solve time at N=7 on 32^3 elements, FP64 vs mixed.
+
+One step = one application of the Helmholtz operator sem_ax to the 16.8M-node
+deformed mesh (32^3 elements, N=7, interior vertices perturbed by up to 10%,
+u uniform in [-1,1] per unique node, h1 = 0.01, h2 = 1/dt with dt = 1e-3).
+The primary value is the FP64 operator's throughput in GDOF/s (local nodes
+per second); the FP32 operator, the FP64 and mixed-precision PCG solves of
+the pressure-Poisson workload and an end-to-end (host buffers) figure are
+reported beside it.  Inputs (u 134 MB, geometry 940 MB) exceed the 129 MB L2,
+so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ORDER, NEL, PERTURB, H1, H2 = 7, (32, 32, 32), 0.1, 0.01, 1000.0
+METRIC = "sem_ax GDOF/s & PCG solve ms at N=7, 32^3 elems: mixed vs FP64, 1 GB300"
+# algorithmic bytes per local node of one operator application
+BYTES_F64 = 72  # read u 8 + G 48 + B 8, write w 8
+BYTES_F32 = 36
+FLOPS_PER_NODE = 12 * (N_ORDER + 1) + 21
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "src": "measured",
+                "sm_max_mhz": d.get("sm_max_mhz", 2070.0)}
+    return {"hbm_gbs": 6800.0, "src": "fallback", "sm_max_mhz": 2070.0}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].strip().lower() == "active"})
+        loaded = [s for s in sm if s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle's operator on the host cores, on a 16^3-element sample of
+    the same deformed N=7 mesh, repeated for about `seconds`."""
+    import numpy as np
+
+    import oracle
+    from paper_2608_24348_gb300 import inputs
+    nel = (16, 16, 16)
+    v = inputs.box_vertices(nel, (2 * math.pi,) * 3, perturb=PERTURB)
+    m = oracle.Mesh(N_ORDER, nel, v)
+    u = inputs.unique_uniform_field(N_ORDER, nel, seed=inputs.SEED_FIELD)
+    m.ax(u, H1, H2)
+    t0 = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t0 < seconds or reps < 1:
+        m.ax(u, H1, H2)
+        reps += 1
+    dt = time.perf_counter() - t0
+    return {"value": m.nL * reps / dt / 1e9, "unit": "GDOF/s", "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle sem_ax on a 16^3-element N=7 deformed mesh "
+                      f"({m.nL} nodes), {reps} applications in {dt:.1f} s"}, reps, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    per = max(2.0, min(20.0, 60.0 / max(1, args.steps)))
+    vals = []
+    info = None
+    for _ in range(args.warmup):
+        cpu_baseline(seconds=0.5)
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        info, reps, dt = cpu_baseline(seconds=per)
+        vals.append(info["value"])
+    wall = time.perf_counter() - t_all
+    v = statistics.median(vals)
+    cb = dict(info)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wall / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "sem_ax, 16^3-element sample of the 32^3 N=7 deformed mesh "
+                                   "(FP64 CPU oracle)", "N": N_ORDER},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_kernel(fn, steps, warmup, stream, ws):
+    """Events around every step on `stream`; barrier + sync on both sides."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(steps):
+            fn()
+            ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    total = ev[0].elapsed_time(ev[steps])
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    return per, total
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2608_24348_gb300 import inputs, sem
+
+    dev = torch.device("cuda", local)
+    pk = peaks()
+    v = inputs.box_vertices(NEL, (2 * math.pi,) * 3, perturb=PERTURB)
+    ctx = sem.Ctx(N_ORDER, NEL, (2 * math.pi,) * 3, (1, 1, 1), vertices=v)
+    nL = ctx.nL
+    u_h = inputs.unique_uniform_field(N_ORDER, NEL, seed=inputs.SEED_FIELD)
+    u64 = torch.from_numpy(u_h).to(dev)
+    w64 = torch.empty_like(u64)
+    u32 = u64.float()
+    w32 = torch.empty_like(u32)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+
+    clocks = Clocks(local)
+    f64 = lambda: ctx.ax(u64, w64, H1, H2, "f64", stream=sp)
+    f32 = lambda: ctx.ax(u32, w32, H1, H2, "f32", stream=sp)
+    clocks.start()
+    per64, tot64 = time_kernel(f64, args.steps, args.warmup, stream, ws)
+    clk = clocks.stop()
+    per32, tot32 = time_kernel(f32, args.steps, args.warmup, stream, ws)
+    tot64 = barrier_max(tot64, ws)
+    tot32 = barrier_max(tot32, ws)
+    ms64 = tot64 / args.steps
+    ms32 = tot32 / args.steps
+    gdof64 = ws * nL / (ms64 * 1e-3) / 1e9
+    gdof32 = ws * nL / (ms32 * 1e-3) / 1e9
+    avg64 = statistics.mean(per64)
+    avg32 = statistics.mean(per32)
+
+    # end to end through the C ABI with pinned host buffers
+    uh = torch.from_numpy(u_h).pin_memory()
+    wh = torch.empty_like(uh).pin_memory()
+    ctx.ax(uh, wh, H1, H2, "f64", stream=sp)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ne = max(3, min(args.steps, 10))
+    for _ in range(ne):
+        ctx.ax(uh, wh, H1, H2, "f64", stream=sp)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ne
+    e2e_s = barrier_max(e2e_s, ws)
+
+    line = {
+        "metric": METRIC, "value": gdof64, "unit": "GDOF/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "sem_ax FP64, 32^3 elements N=7 deformed (16.8M local nodes), "
+                               "h1=0.01 h2=1000", "N": N_ORDER, "elements": list(NEL),
+                   "local_nodes": nL, "l2": "inputs larger than L2 (1.2 GB per application)"},
+        "roofline": {"bound": "hbm", "achieved": BYTES_F64 * nL / (avg64 * 1e-3) / 1e9,
+                     "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": BYTES_F64 * nL / (avg64 * 1e-3) / 1e9 / pk["hbm_gbs"],
+                     "traffic": None, "peak_src": pk["src"], "kernel": "k_ax<8,double>"},
+        "mixed": {"sem_ax_f32_gdofs": gdof32, "ms_per_app": ms32,
+                  "roofline": {"bound": "hbm", "achieved": BYTES_F32 * nL / (avg32 * 1e-3) / 1e9,
+                               "peak": pk["hbm_gbs"], "unit": "GB/s",
+                               "frac": BYTES_F32 * nL / (avg32 * 1e-3) / 1e9 / pk["hbm_gbs"]},
+                  "speedup_vs_f64": ms64 / ms32},
+        "e2e": {"value": ws * nL / e2e_s / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": 8 * nL,
+                "d2h_bytes_per_step": 8 * nL},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        cb, _, _ = cpu_baseline(seconds=12.0)
+        line["cpu_baseline"] = cb
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * sem.h -- C ABI of libsem: the GB300 (sm_103a) spectral-element hot path.
+ *
+ * The operations are those of a matrix-free SEM Navier-Stokes solver in the
+ * P_N-P_N splitting (Chen, Muensch, Iakymchuk, "Mixed-Precision SEM-Based CFD
+ * Simulations on GPUs: A Taylor-Green Vortex case"): the Helmholtz operator
+ * ax_helm (Sec. 4, Table 2 rows B-6/B-7), the gather-scatter direct-stiffness
+ * sum (Sec. 2, "gather/scatter" in the other-operations block), the Jacobi
+ * preconditioned CG of the velocity solve with higher-precision reductions
+ * (Sec. 1.1; Sec. 2, reductions capped at fp64), and the Taylor-Green vortex
+ * time step with dealiased advection (Sec. 3; Sec. 1.1 Fig. 3 hotspots).
+ * The paper prints no SEM formula; the operators are the textbook ones
+ * (Deville, Fischer & Mund 2002) restated in each declaration below.
+ *
+ * Conventions for every entry point:
+ *  - Field arguments are E-vectors: E*(N+1)^3 contiguous values, layout
+ *    [E][N+1][N+1][N+1] with i (the r direction) fastest and element
+ *    e = ex + nelx*(ey + nely*ez).  Their element type follows the sem_dtype
+ *    argument: double for SEM_F64, float for the other three.
+ *  - Field pointers may be device memory (the fast path) or host memory
+ *    (pinned or pageable); host buffers are staged through device buffers
+ *    owned by the context, allocated on the first such call.
+ *  - The caller owns every field buffer.  The library owns the geometry and
+ *    the solver workspaces; it allocates only in sem_setup, sem_tgv_init and
+ *    the first host-pointer call, never inside a device-pointer hot call.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *    device-pointer calls are asynchronous and stream ordered.
+ *  - Every int-returning call returns SEM_OK (0) or a negative SEM_ERR_*.
+ *    No call aborts, traps or throws across the ABI.
+ *  - One context may be used by one host thread at a time.
+ *  - Supported polynomial orders: 1 <= N <= 15.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SEM_API __attribute__((visibility("default")))
+#else
+#define SEM_API
+#endif
+
+#define SEM_OK 0
+#define SEM_ERR_ARG (-1)           /* invalid argument (size, order, pointer, dtype) */
+#define SEM_ERR_CUDA (-2)          /* a CUDA runtime call failed */
+#define SEM_ERR_NOMEM (-3)         /* device or host allocation failed */
+#define SEM_ERR_BAD_MESH (-4)      /* a non-positive Jacobian determinant */
+#define SEM_ERR_NOT_CONVERGED (-5) /* maxit reached; x holds the last iterate */
+#define SEM_ERR_BREAKDOWN (-6)     /* <p,Ap> <= 0 or a non-finite residual */
+#define SEM_ERR_TIMEOUT (-7)       /* a bounded device-side wait gave up */
+
+typedef enum {
+    SEM_F64 = 0,     /* FP64 storage and arithmetic */
+    SEM_F32 = 1,     /* FP32 storage and arithmetic */
+    SEM_BF16_TC = 2, /* FP32 storage, BF16 tensor-core contractions, FP32 accumulation */
+    SEM_F16_TC = 3   /* FP32 storage, FP16 tensor-core contractions, FP32 accumulation */
+} sem_dtype;
+
+typedef struct sem_ctx sem_ctx;
+typedef struct sem_tgv sem_tgv;
+
+typedef struct {
+    int N, nelx, nely, nelz;
+    int periodic[3];
+    int64_t E;      /* elements */
+    int64_t nL;     /* local (element-duplicated) nodes = E (N+1)^3 */
+    int64_t nG;     /* unique nodes */
+    double volume;  /* sum of the local mass B */
+} sem_ctx_info;
+
+/* Build a context on the current CUDA device (Sec. 1.1 Fig. 3, pre-processing).
+ * N: polynomial order, 1..15.  nelx, nely, nelz >= 1 elements per direction.
+ * extents: box lengths (host, 3 doubles; origin at 0) used when vertices is
+ * NULL.  periodic: 3 flags (host).  vertices: NULL for a uniform box, else a
+ * host array of (nelz+1)(nely+1)(nelx+1) points, 3 doubles each, laid out
+ * [K][J][I][xyz]; element (ex,ey,ez) is the trilinear map of its 8 corners.
+ * Periodic directions need flat, translation-equivalent boundary planes.
+ * Computes on the device, in FP64: GLL nodes/weights, D, node coordinates,
+ * J^{-1}, the six geometric factors G and the mass B (plus FP32 copies).
+ * Errors: SEM_ERR_ARG, SEM_ERR_BAD_MESH (some |J| <= 0), SEM_ERR_NOMEM,
+ * SEM_ERR_CUDA.  On success *out owns all library memory. */
+SEM_API int sem_setup(int N, int nelx, int nely, int nelz, const double extents[3],
+              const int periodic[3], const double *vertices, sem_ctx **out);
+
+/* Free a context (NULL is allowed).  Synchronises the device first. */
+SEM_API void sem_destroy(sem_ctx *ctx);
+
+/* Sizes of a context. */
+SEM_API int sem_get_info(const sem_ctx *ctx, sem_ctx_info *info);
+
+/* Message for an error code (static string). */
+SEM_API const char *sem_strerror(int code);
+
+/* Text of the last CUDA runtime error seen by this host thread (for
+ * SEM_ERR_CUDA); empty if none. */
+SEM_API const char *sem_last_cuda_error(void);
+
+/* Node coordinates: xyz holds 3 E-vectors (x, then y, then z), FP64. */
+SEM_API int sem_coords(sem_ctx *ctx, double *xyz, void *stream);
+
+/* Geometric factors as computed by sem_setup: out holds 7 E-vectors, FP64, in
+ * the order G11, G22, G33, G12, G13, G23, B, where
+ *   B = w_i w_j w_k |J|,  G_ab = B sum_c (dr_a/dx_c)(dr_b/dx_c). */
+SEM_API int sem_geom(sem_ctx *ctx, double *out, void *stream);
+
+/* Local Helmholtz operator, ax_helm (Sec. 4, Table 2 rows B-6, B-7):
+ *   w_e = h1 sum_{a,b} D_a^T G_ab D_b u_e + h2 B u_e   for every element e,
+ * with D_r = I x I x D, D_s = I x D x I, D_t = D x I x I.  Not assembled
+ * (follow with sem_dssum).  u and w must not overlap.  dtype selects the
+ * arithmetic; SEM_BF16_TC / SEM_F16_TC round u and the intermediate fluxes
+ * to 16 bits for tensor-core contractions with FP32 accumulation. */
+SEM_API int sem_ax(sem_ctx *ctx, const void *u, void *w, double h1, double h2, sem_dtype dtype,
+           void *stream);
+
+/* Direct-stiffness sum in place (Sec. 2, gather/scatter): every local copy of
+ * a unique node receives the sum of all its copies (Q Q^T u).  Deterministic:
+ * no atomics, a fixed summation order per unique node.  dtype SEM_F64 (double)
+ * or SEM_F32 (float; the TC dtypes are treated as SEM_F32). */
+SEM_API int sem_dssum(sem_ctx *ctx, void *u, sem_dtype dtype, void *stream);
+
+/* Inverse assembled Jacobi diagonal, FP64 E-vector:
+ *  minv = 1 / dssum( h1 [ sum_l D_li^2 G11(l,j,k) + sum_l D_lj^2 G22(i,l,k)
+ *                        + sum_l D_lk^2 G33(i,j,l) + 2 D_ii D_jj G12
+ *                        + 2 D_ii D_kk G13 + 2 D_jj D_kk G23 ] + h2 B ). */
+SEM_API int sem_jacobi(sem_ctx *ctx, double h1, double h2, double *minv, void *stream);
+
+/* Solver options.  tol: stopping tolerance on the assembled residual norm
+ * ||r|| = sqrt(sum_local r^2 / mult); relative to ||b|| unless abs_tol != 0.
+ * inner: the operator precision; SEM_F64 runs plain FP64 PCG, the other three
+ * run FP64 iterative refinement around an inner PCG in that precision
+ * (vectors FP32, dot products FP64) with relative tolerance inner_tol.
+ * maxit bounds the PCG iterations (total inner iterations for refinement),
+ * max_outer the refinement steps. */
+typedef struct {
+    double tol;
+    int abs_tol;
+    int maxit;
+    sem_dtype inner;
+    double inner_tol;
+    int max_outer;
+} sem_solve_opts;
+
+/* Filled after the stream is synchronised. */
+typedef struct {
+    int status;         /* SEM_OK, SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT */
+    int iters;          /* PCG iterations (sum of inner iterations under refinement) */
+    int outer_iters;    /* refinement steps (0 for plain FP64 PCG) */
+    double final_rnorm; /* FP64 assembled residual norm at exit */
+    double bnorm;       /* FP64 assembled norm of the (mean-free when h2 == 0) RHS */
+} sem_solve_info;
+
+/* Default options: tol 1e-10 relative, maxit 20000, inner SEM_F64,
+ * inner_tol 1e-4, max_outer 50. */
+SEM_API void sem_solve_opts_default(sem_solve_opts *opts);
+
+/* Jacobi-PCG on dssum(A) x = b with A = h1 D^T G D + h2 B (Sec. 1.1: CG with
+ * the Jacobi preconditioner; Sec. 2: reductions in fp64).  b: assembled RHS
+ * (continuous E-vector), FP64.  x: FP64 E-vector, initial guess on entry,
+ * solution (or last iterate) on exit.  With h2 == 0 the constants span the
+ * null space: b loses its mean before the iteration and x its B-weighted mean
+ * after it.  The whole solve is one persistent cooperative kernel launch
+ * (graph capturable); every wait inside it is bounded (SEM_ERR_TIMEOUT).
+ * info: NULL for a fully asynchronous call (read it later with
+ * sem_last_solve_info after synchronising), else the call synchronises the
+ * stream, fills *info and returns info->status. */
+SEM_API int sem_pcg_solve(sem_ctx *ctx, const double *b, double *x, double h1, double h2,
+                  const sem_solve_opts *opts, sem_solve_info *info, void *stream);
+
+/* Status of the last solve enqueued on ctx (valid after a stream sync). */
+SEM_API int sem_last_solve_info(sem_ctx *ctx, sem_solve_info *info);
+
+/* nprob independent solves in one persistent launch.  ctxs[p], b[p], x[p],
+ * h1[p], h2[p] as in sem_pcg_solve (device pointers only); contexts may
+ * differ in N and element count and may repeat.  infos (host, nprob entries)
+ * may be NULL for an asynchronous call.  All problems use opts. */
+SEM_API int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const double *const *b,
+                          double *const *x, const double *h1, const double *h2,
+                          const sem_solve_opts *opts, sem_solve_info *infos, void *stream);
+
+/* ---- Taylor-Green vortex stepper (Sec. 3) ---- */
+
+typedef struct {
+    double t, ke, enstrophy;   /* KE = 1/(2V) sum_local B |u|^2, enstrophy likewise with curl u */
+    int iters[4];              /* pressure, u, v, w solver iterations */
+    int status;
+} sem_tgv_diag;
+
+/* Stepper on a periodic context.  nu: viscosity; dt: time step.  op: operator
+ * precision (SEM_F64, or SEM_F32 = FP32 operators, convection and inner
+ * solves with FP64 refinement, histories and diagnostics).  vel / pres:
+ * solver options for the velocity Helmholtz and pressure Poisson solves. */
+SEM_API int sem_tgv_init(sem_ctx *ctx, double nu, double dt, sem_dtype op, const sem_solve_opts *vel,
+                 const sem_solve_opts *pres, sem_tgv **out);
+
+/* Set the state at history level (0 = u^n, 1 = u^{n-1}, 2 = u^{n-2}) from
+ * FP64 E-vectors u, v, w (and p for level 0; may be NULL); step is the number
+ * of steps already taken (selects the startup order), t the time. */
+SEM_API int sem_tgv_set(sem_tgv *tgv, int level, const double *u, const double *v, const double *w,
+                const double *p, int step, double t, void *stream);
+
+/* Advance nsteps P_N-P_N steps (BDF3/EXT3, 3/2-rule dealiasing).  diag: host
+ * array of nsteps entries or NULL; when given, the call synchronises. */
+SEM_API int sem_tgv_step(sem_tgv *tgv, int nsteps, sem_tgv_diag *diag, void *stream);
+
+/* Copy out u^n, v^n, w^n, p^n (FP64 E-vectors; any may be NULL). */
+SEM_API int sem_tgv_get(sem_tgv *tgv, double *u, double *v, double *w, double *p, void *stream);
+
+/* Kinetic energy and enstrophy of the current state (host doubles). */
+SEM_API int sem_tgv_energy(sem_tgv *tgv, double *ke, double *enstrophy, void *stream);
+
+SEM_API void sem_tgv_destroy(sem_tgv *tgv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEM_H */

@@ -143,6 +143,11 @@ def interp(N: int, x) -> np.ndarray:
     return J
 
 
+def threads() -> int:
+    """OpenMP threads the oracle uses."""
+    return lib().orc_threads()
+
+
 def dealias_m(N: int) -> int:
     """Points per direction of the 3/2-rule dealiasing grid."""
     return lib().orc_dealias_m(N)

@@ -36,6 +36,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_ERR_ARG -1
@@ -44,6 +47,16 @@
 #define ORC_ERR_BREAKDOWN -6
 
 #define ORC_NMAX 15
+
+/* Number of OpenMP threads the oracle runs with. */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* 1-D polynomial tools                                                      */
