@@ -136,7 +136,9 @@ SEM_API int sem_jacobi(sem_ctx *ctx, double h1, double h2, double *minv, void *s
  * run FP64 iterative refinement around an inner PCG in that precision
  * (vectors FP32, dot products FP64) with relative tolerance inner_tol.
  * maxit bounds the PCG iterations (total inner iterations for refinement),
- * max_outer the refinement steps. */
+ * max_outer the refinement steps.  wait_timeout_s bounds every device-side
+ * wait of the persistent solver (<= 0 selects 10 s); when one runs out the
+ * solve ends with SEM_ERR_TIMEOUT and the context stays usable. */
 typedef struct {
     double tol;
     int abs_tol;
@@ -144,6 +146,7 @@ typedef struct {
     sem_dtype inner;
     double inner_tol;
     int max_outer;
+    double wait_timeout_s;
 } sem_solve_opts;
 
 /* Filled after the stream is synchronised. */
@@ -156,7 +159,7 @@ typedef struct {
 } sem_solve_info;
 
 /* Default options: tol 1e-10 relative, maxit 20000, inner SEM_F64,
- * inner_tol 1e-4, max_outer 50. */
+ * inner_tol 1e-4, max_outer 50, wait_timeout_s 0 (10 s). */
 SEM_API void sem_solve_opts_default(sem_solve_opts *opts);
 
 /* Jacobi-PCG on dssum(A) x = b with A = h1 D^T G D + h2 B (Sec. 1.1: CG with

@@ -143,6 +143,20 @@ def interp(N: int, x) -> np.ndarray:
     return J
 
 
+def fourier(K, cc, cs, x, y, z):
+    """sum_m cc_m cos(k_m . x) + cs_m sin(k_m . x) at the given points."""
+    K = np.ascontiguousarray(K, dtype=np.int64)
+    cc, cs = _f64(cc), _f64(cs)
+    x, y, z = (_f64(v).reshape(-1) for v in (x, y, z))
+    out = np.zeros(x.size)
+    kmax = int(np.abs(K).max())
+    rc = lib().orc_fourier(ctypes.c_long(len(K)), K.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                           _p(cc), _p(cs), ctypes.c_long(x.size), _p(x), _p(y), _p(z), kmax, _p(out))
+    if rc:
+        raise ValueError(f"orc_fourier -> {rc}")
+    return out
+
+
 def threads() -> int:
     """OpenMP threads the oracle uses."""
     return lib().orc_threads()

@@ -1031,3 +1031,50 @@ int orc_tgv_step(void *hnd, int nsteps, double *diag)
     free(bp); free(rhs); free(gr);
     return rc_all;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Analytic right-hand side: a finite Fourier series at given points         */
+/* ------------------------------------------------------------------------ */
+
+/* out[p] = sum_m cc[m] cos(k_m . x_p) + cs[m] sin(k_m . x_p), k_m integer with
+ * |k| components <= kmax; e^{i k.x} built from tabulated integer powers of
+ * e^{ix}, e^{iy}, e^{iz}.  (Input generation for the pressure-Poisson
+ * workload: the divergence of a random smooth velocity field.) */
+int orc_fourier(long nm, const long *K, const double *cc, const double *cs, long npts,
+                const double *x, const double *y, const double *z, int kmax, double *out)
+{
+    if (kmax < 0 || kmax > 32) return ORC_ERR_ARG;
+    int w = 2 * kmax + 1;
+#pragma omp parallel
+    {
+        double *tab = malloc(sizeof(double) * 6 * w);
+#pragma omp for schedule(static)
+        for (long p = 0; p < npts; ++p) {
+            const double c3[3] = {x[p], y[p], z[p]};
+            for (int d = 0; d < 3; ++d) {
+                double *re = tab + (2 * d) * w, *im = re + w;
+                double cr = cos(c3[d]), ci = sin(c3[d]);
+                re[kmax] = 1.0; im[kmax] = 0.0;
+                for (int q = 1; q <= kmax; ++q) {
+                    re[kmax + q] = re[kmax + q - 1] * cr - im[kmax + q - 1] * ci;
+                    im[kmax + q] = re[kmax + q - 1] * ci + im[kmax + q - 1] * cr;
+                    re[kmax - q] = re[kmax + q];
+                    im[kmax - q] = -im[kmax + q];
+                }
+            }
+            double s = 0.0;
+            for (long m = 0; m < nm; ++m) {
+                int a = (int)K[3 * m] + kmax, b = (int)K[3 * m + 1] + kmax, cidx = (int)K[3 * m + 2] + kmax;
+                double ar = tab[a], ai = tab[w + a];
+                double br = tab[2 * w + b], bi = tab[3 * w + b];
+                double zr = tab[4 * w + cidx], zi = tab[5 * w + cidx];
+                double tr = ar * br - ai * bi, ti = ar * bi + ai * br;
+                double er = tr * zr - ti * zi, ei = tr * zi + ti * zr;
+                s += cc[m] * er + cs[m] * ei;
+            }
+            out[p] = s;
+        }
+        free(tab);
+    }
+    return ORC_OK;
+}

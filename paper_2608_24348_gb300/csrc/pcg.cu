@@ -1,34 +1,282 @@
-// pcg.cu -- Jacobi PCG, FP64 iterative refinement, batched solves.
-#include "common.cuh"
+// pcg.cu -- host side of the persistent PCG / iterative-refinement solver.
+#include <string.h>
 
-struct sem_solve_state {
-    int status, iters, outer_iters, pad;
-    double rnorm, bnorm;
+#include <vector>
+
+#include "solver.cuh"
+
+GsDesc sem_gs_desc(const sem_ctx *c);  // ops.cu
+int sem_alloc_ws(sem_ctx *c, int slot);  // setup.cu
+
+// Per-order kernels (solve_npXX.cu), up to 8 problems of one order.
+#define SEM_DECL_NP(NPV) int sem_solve_launch_np##NPV(const SolveParams<8> &, int, long long, cudaStream_t);
+SEM_DECL_NP(2) SEM_DECL_NP(3) SEM_DECL_NP(4) SEM_DECL_NP(5) SEM_DECL_NP(6) SEM_DECL_NP(7)
+SEM_DECL_NP(8) SEM_DECL_NP(9) SEM_DECL_NP(10) SEM_DECL_NP(11) SEM_DECL_NP(12) SEM_DECL_NP(13)
+SEM_DECL_NP(14) SEM_DECL_NP(15) SEM_DECL_NP(16)
+#undef SEM_DECL_NP
+// Mixed-order kernel for N in {5, 7, 9} (solve_multi.cu), up to 64 problems.
+int sem_solve_launch_multi(const SolveParams<SEM_MAXP> &, int, long long, cudaStream_t);
+
+typedef int (*launch8_fn)(const SolveParams<8> &, int, long long, cudaStream_t);
+static const launch8_fn k_launch8[17] = {
+    nullptr, nullptr, sem_solve_launch_np2, sem_solve_launch_np3, sem_solve_launch_np4,
+    sem_solve_launch_np5, sem_solve_launch_np6, sem_solve_launch_np7, sem_solve_launch_np8,
+    sem_solve_launch_np9, sem_solve_launch_np10, sem_solve_launch_np11, sem_solve_launch_np12,
+    sem_solve_launch_np13, sem_solve_launch_np14, sem_solve_launch_np15, sem_solve_launch_np16};
+
+struct SolveStateHost {
+    SyncState sync;
+    PState st[SEM_MAXP];
+    int sched[SEM_MAXP * 2 + 2];
 };
 
-int sem_solve_state_bytes() { return (int)sizeof(sem_solve_state) * 64; }
+int sem_solve_state_bytes() { return (int)sizeof(SolveStateHost); }
+
+size_t sem_partials_bytes(int num_sms)
+{
+    return sizeof(double) * (size_t)num_sms * SEM_SOLVE_MAX_GRID_PER_SM * SEM_MAXP * 3;
+}
 
 extern "C" void sem_solve_opts_default(sem_solve_opts *o)
 {
+    if (!o) return;
     o->tol = 1e-10;
     o->abs_tol = 0;
     o->maxit = 20000;
     o->inner = SEM_F64;
     o->inner_tol = 1e-4;
     o->max_outer = 50;
+    o->wait_timeout_s = 0.0;
 }
 
-extern "C" int sem_pcg_solve(sem_ctx *, const double *, double *, double, double,
-                             const sem_solve_opts *, sem_solve_info *, void *)
+static int ne_for(int n) { return (256 / (n * n)) > 0 ? 256 / (n * n) : 1; }
+
+// Element groups of the TC path use one warp per element.
+static int TcNE(int n) { return n <= 8 ? 8 : 4; }
+
+static void fill_desc(const sem_ctx *c, const sem_ws &ws, const double *b, double *x, double h1,
+                      double h2, bool mixed, bool tc, ProbDesc &d)
 {
-    return SEM_ERR_ARG;
+    memset(&d, 0, sizeof(d));
+    d.n = c->n;
+    d.NE = ne_for(c->n);
+    d.NE32 = tc ? TcNE(c->n) : d.NE;
+    d.singular = (h2 == 0.0);
+    d.E = c->E;
+    d.nL = c->nL;
+    d.nG = c->nG;
+    d.gs = sem_gs_desc(c);
+    d.volume = c->volume;
+    d.h1 = h1;
+    d.h2 = h2;
+    d.geo64 = c->geo64;
+    d.geo32 = c->geo32;
+    d.D64 = c->tab64 + 2 * c->n;
+    d.D32 = c->tab32 + 2 * c->n;
+    d.b = b;
+    d.x = x;
+    d.r = ws.r;
+    d.p = ws.p;
+    d.w = ws.w;
+    d.minv = ws.minv;
+    if (mixed) {
+        d.r32 = ws.r32;
+        d.p32 = ws.p32;
+        d.w32 = ws.w32;
+        d.d32 = ws.d32;
+        d.minv32 = ws.minv32;
+    }
 }
 
-extern "C" int sem_last_solve_info(sem_ctx *, sem_solve_info *) { return SEM_ERR_ARG; }
-
-extern "C" int sem_pcg_solve_batched(int, sem_ctx *const *, const double *const *, double *const *,
-                                     const double *, const double *, const sem_solve_opts *,
-                                     sem_solve_info *, void *)
+template <int MAXP>
+static void fill_common(SolveParams<MAXP> &p, sem_ctx *owner, const sem_solve_opts &o, int nprob)
 {
-    return SEM_ERR_ARG;
+    p.nprob = nprob;
+    p.mixed = o.inner != SEM_F64;
+    p.inner_tc = o.inner == SEM_BF16_TC ? 1 : (o.inner == SEM_F16_TC ? 2 : 0);
+    p.abs_tol = o.abs_tol;
+    p.maxit = o.maxit;
+    p.max_outer = o.max_outer;
+    p.tol = o.tol;
+    p.inner_tol = o.inner_tol;
+    const double tmo = o.wait_timeout_s > 0 ? o.wait_timeout_s : 10.0;
+    p.timeout_ns = (long long)(tmo * 1e9);
+    SolveStateHost *S = (SolveStateHost *)owner->solve_dev;
+    p.sync = &S->sync;
+    p.st = S->st;
+    p.sched = S->sched;
+    p.partials = (double *)owner->partials;
+}
+
+static long long max_items(const ProbDesc *d, int np)
+{
+    long long m = 1;
+    for (int p = 0; p < np; ++p) {
+        long long a = (d[p].nL + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS;
+        if (a > m) m = a;
+    }
+    return m;
+}
+
+static int validate_opts(const sem_solve_opts &o)
+{
+    if (!(o.tol >= 0) || o.maxit < 0 || o.max_outer < 0) return SEM_ERR_ARG;
+    if (o.inner < SEM_F64 || o.inner > SEM_F16_TC) return SEM_ERR_ARG;
+    if (o.inner != SEM_F64 && !(o.inner_tol > 0 && o.inner_tol < 1)) return SEM_ERR_ARG;
+    return SEM_OK;
+}
+
+// Enqueue one launch for problems `idx` (all on owner's state buffers).
+static int enqueue(sem_ctx *owner, const sem_solve_opts &o, const ProbDesc *d, int np,
+                   cudaStream_t s)
+{
+    SEM_CUDA(cudaMemsetAsync(owner->solve_dev, 0, sizeof(SolveStateHost), s));
+    const long long mi = max_items(d, np);
+    bool same = true;
+    for (int p = 1; p < np; ++p) same &= (d[p].n == d[0].n);
+    int rc;
+    if (same && np <= 8) {
+        SolveParams<8> prm;
+        memset(&prm, 0, sizeof(prm));
+        fill_common(prm, owner, o, np);
+        for (int p = 0; p < np; ++p) prm.prob[p] = d[p];
+        rc = k_launch8[d[0].n](prm, owner->num_sms, mi, s);
+    } else {
+        SolveParams<SEM_MAXP> *prm = new SolveParams<SEM_MAXP>();
+        fill_common(*prm, owner, o, np);
+        for (int p = 0; p < np; ++p) prm->prob[p] = d[p];
+        rc = sem_solve_launch_multi(*prm, owner->num_sms, mi, s);
+        delete prm;
+    }
+    if (rc) return rc;
+    SEM_CUDA(cudaMemcpyAsync(owner->solve_host, owner->solve_dev, sizeof(SolveStateHost),
+                             cudaMemcpyDeviceToHost, s));
+    return SEM_OK;
+}
+
+static void read_info(const sem_ctx *owner, int p, sem_solve_info *info)
+{
+    const SolveStateHost *H = (const SolveStateHost *)owner->solve_host;
+    const PState &S = H->st[p];
+    info->status = H->sync.err ? H->sync.err : S.status;
+    info->iters = S.iters;
+    info->outer_iters = S.outer;
+    info->final_rnorm = S.rnorm;
+    info->bnorm = S.bnorm;
+}
+
+extern "C" int sem_last_solve_info(sem_ctx *c, sem_solve_info *info)
+{
+    if (!c || !info) return SEM_ERR_ARG;
+    read_info(c, 0, info);
+    return SEM_OK;
+}
+
+// Device-pointer solve used by the stepper.
+int sem_pcg_solve_dev(sem_ctx *c, int slot, const double *b, double *x, double h1, double h2,
+                      const sem_solve_opts &o, cudaStream_t s)
+{
+    const bool mixed = o.inner != SEM_F64;
+    const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC;
+    if (tc && c->n > 10) return SEM_ERR_ARG;
+    ProbDesc d;
+    fill_desc(c, c->ws[slot], b, x, h1, h2, mixed, tc, d);
+    return enqueue(c, o, &d, 1, s);
+}
+
+extern "C" int sem_pcg_solve(sem_ctx *c, const double *b, double *x, double h1, double h2,
+                             const sem_solve_opts *opts, sem_solve_info *info, void *stream)
+{
+    if (!c || !b || !x) return SEM_ERR_ARG;
+    sem_solve_opts o;
+    sem_solve_opts_default(&o);
+    if (opts) o = *opts;
+    int rc = validate_opts(o);
+    if (rc) return rc;
+    if (!(h1 >= 0) || !(h2 >= 0) || (h1 == 0 && h2 == 0)) return SEM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * c->nL;
+    const void *bd;
+    void *xd;
+    int bh, xh;
+    rc = sem_stage_in(c, b, bytes, 0, s, &bd, &bh);
+    if (rc) return rc;
+    const void *xin;
+    rc = sem_stage_in(c, x, bytes, 1, s, &xin, &xh);
+    if (rc) return rc;
+    xd = (void *)xin;
+    rc = sem_pcg_solve_dev(c, 0, (const double *)bd, (double *)xd, h1, h2, o, s);
+    if (rc) return rc;
+    if (xh) SEM_CUDA(cudaMemcpyAsync(x, xd, bytes, cudaMemcpyDeviceToHost, s));
+    if (info || bh || xh) SEM_CUDA(cudaStreamSynchronize(s));
+    if (info) {
+        read_info(c, 0, info);
+        return info->status;
+    }
+    return SEM_OK;
+}
+
+extern "C" int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const double *const *b,
+                                     double *const *x, const double *h1, const double *h2,
+                                     const sem_solve_opts *opts, sem_solve_info *infos,
+                                     void *stream)
+{
+    if (nprob < 1 || nprob > SEM_MAXP || !ctxs || !b || !x || !h1 || !h2) return SEM_ERR_ARG;
+    sem_solve_opts o;
+    sem_solve_opts_default(&o);
+    if (opts) o = *opts;
+    int rc = validate_opts(o);
+    if (rc) return rc;
+    const bool mixed = o.inner != SEM_F64;
+    const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<ProbDesc> d(nprob);
+    std::vector<int> slot(nprob, 0);
+    for (int p = 0; p < nprob; ++p) {
+        sem_ctx *c = ctxs[p];
+        if (!c || !b[p] || !x[p]) return SEM_ERR_ARG;
+        if (!(h1[p] >= 0) || !(h2[p] >= 0) || (h1[p] == 0 && h2[p] == 0)) return SEM_ERR_ARG;
+        if (tc && c->n > 10) return SEM_ERR_ARG;
+        if (!sem_is_device_ptr(b[p]) || !sem_is_device_ptr(x[p])) return SEM_ERR_ARG;
+        for (int q = 0; q < p; ++q) slot[p] += (ctxs[q] == c);
+        if (slot[p] >= 4) return SEM_ERR_ARG;
+        while (c->nws <= slot[p]) {  // first use of a repeated context: one more workspace
+            rc = sem_alloc_ws(c, c->nws);
+            if (rc) return rc;
+            c->nws += 1;
+        }
+        fill_desc(c, c->ws[slot[p]], b[p], x[p], h1[p], h2[p], mixed, tc, d[p]);
+    }
+    sem_ctx *owner = ctxs[0];
+    bool multi_ok = true, same = true;
+    for (int p = 0; p < nprob; ++p) {
+        multi_ok &= (d[p].n == 6 || d[p].n == 8 || d[p].n == 10);
+        same &= (d[p].n == d[0].n);
+    }
+    if ((same && nprob <= 8) || multi_ok) {
+        rc = enqueue(owner, o, d.data(), nprob, s);
+        if (rc) return rc;
+        if (infos) {
+            SEM_CUDA(cudaStreamSynchronize(s));
+            int worst = SEM_OK;
+            for (int p = 0; p < nprob; ++p) {
+                read_info(owner, p, &infos[p]);
+                if (infos[p].status != SEM_OK && worst == SEM_OK) worst = infos[p].status;
+            }
+            return worst;
+        }
+        return SEM_OK;
+    }
+    // other order mixes: one launch per problem, in order
+    int worst = SEM_OK;
+    for (int p = 0; p < nprob; ++p) {
+        rc = enqueue(owner, o, &d[p], 1, s);
+        if (rc) return rc;
+        if (infos) {
+            SEM_CUDA(cudaStreamSynchronize(s));
+            read_info(owner, 0, &infos[p]);
+            if (infos[p].status != SEM_OK && worst == SEM_OK) worst = infos[p].status;
+        }
+    }
+    return infos ? worst : SEM_OK;
 }

@@ -304,7 +304,8 @@ extern "C" void sem_destroy(sem_ctx *c)
     free(c);
 }
 
-int sem_solve_state_bytes();  // pcg.cu
+int sem_solve_state_bytes();             // pcg.cu
+size_t sem_partials_bytes(int num_sms);  // pcg.cu
 
 extern "C" int sem_setup(int N, int nelx, int nely, int nelz, const double extents[3],
                          const int periodic[3], const double *vertices, sem_ctx **out)
@@ -388,6 +389,7 @@ extern "C" int sem_setup(int N, int nelx, int nely, int nelz, const double exten
     SETUP_TRY(cudaMalloc(&c->solve_dev, sem_solve_state_bytes()));
     SETUP_TRY(cudaMemset(c->solve_dev, 0, sem_solve_state_bytes()));
     SETUP_TRY(cudaMallocHost(&c->solve_host, sem_solve_state_bytes()));
+    SETUP_TRY(cudaMalloc(&c->partials, sem_partials_bytes(c->num_sms)));
     memset(c->solve_host, 0, sem_solve_state_bytes());
     SETUP_TRY(cudaDeviceSynchronize());
 #undef SETUP_TRY

@@ -1,0 +1,7 @@
+// solve_np06.cu -- persistent solver kernel for order N = 5 (up to 8 problems).
+#include "solver.cuh"
+
+int sem_solve_launch_np6(const SolveParams<8> &p, int sms, long long mi, cudaStream_t s)
+{
+    return launch_solve<8, 6>(p, sms, mi, s);
+}

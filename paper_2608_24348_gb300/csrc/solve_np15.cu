@@ -1,0 +1,7 @@
+// solve_np15.cu -- persistent solver kernel for order N = 14 (up to 8 problems).
+#include "solver.cuh"
+
+int sem_solve_launch_np15(const SolveParams<8> &p, int sms, long long mi, cudaStream_t s)
+{
+    return launch_solve<8, 15>(p, sms, mi, s);
+}

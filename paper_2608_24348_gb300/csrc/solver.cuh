@@ -1,0 +1,678 @@
+// solver.cuh -- persistent, cooperative Jacobi-PCG / FP64 iterative refinement.
+//
+// One launch runs a whole solve (or a batch of independent solves).  Every
+// problem carries a small state machine; all problems advance together in
+// "grid steps".  In a step each problem executes the work items of its
+// current phase (element groups, chunks of unique nodes or chunks of local
+// nodes), every CTA adds its FP64 partial sums, and a reducing grid barrier
+// ends the step: the last CTA to arrive sums the partials of every problem in
+// a fixed order (deterministic), advances each state machine, publishes the
+// next schedule and releases the others.  Every wait is bounded in time; a
+// CTA that gives up raises SEM_ERR_TIMEOUT and the whole grid exits.
+//
+// Phases of one problem (Sec. 1.1: CG with Jacobi; Sec. 2: dot products and
+// norms reduced in fp64):
+//   JAC    local   minv = local diagonal of A
+//   JACGS  unique  minv = 1/dssum(minv);  sum b  (mean removal when h2 == 0)
+//   AX0    element w = A x                                      (FP64)
+//   R0     unique  r = b' - dssum(w); <r,r>, <r,z>, <b',b'>      (plain PCG)
+//   A      element p = z + beta p; w = A p; <p,w>                (FP64)
+//   C      unique  x += alpha p; r -= alpha dssum(w); <r,r>, <r,z>
+//   R64    unique  r = b' - dssum(w); <r,r>, <b',b'>            (refinement)
+//   INIT32 unique  r32 = r / ||r||; d = 0; <r32,r32>, <r32,z32>
+//   A32    element p32 = z32 + beta p32; w32 = A32 p32; <p32,w32>
+//   C32    unique  d += alpha p32; r32 -= alpha dssum(w32); ...
+//   UPD    local   x += ||r|| d
+//   FINAL  local   sum B x              (h2 == 0: remove the B-weighted mean)
+//   SHIFT  local   x -= sum(B x) / sum(B)
+// The inner product <a,b> = sum_local a b / mult is evaluated over unique
+// nodes, where it is a plain sum; <p, dssum(Ap)> equals sum_local p (Ap)
+// for a continuous p, which lets the element phase produce it directly.
+#pragma once
+
+#include <type_traits>
+
+#include "ax.cuh"
+#include "ax_tc.cuh"
+#include "common.cuh"
+#include "gs.cuh"
+
+#define SEM_MAXP 64
+#define SEM_SOLVE_THREADS 256
+
+enum SolvePhase {
+    PH_JAC = 0, PH_JACGS, PH_AX0, PH_R0, PH_A, PH_C, PH_R64, PH_INIT32, PH_A32, PH_C32, PH_UPD,
+    PH_FINAL, PH_SHIFT, PH_DONE
+};
+
+struct ProbDesc {
+    int n, NE, NE32, singular;  // NE: elements per group (CUDA cores); NE32: inner operator
+    int64_t E, nL, nG;
+    GsDesc gs;
+    double volume, h1, h2;
+    const double *geo64;
+    const float *geo32;
+    const double *D64;
+    const float *D32;
+    const double *b;
+    double *x;
+    double *r, *p, *w, *minv;
+    float *r32, *p32, *w32, *d32, *minv32;
+};
+
+struct PState {
+    int phase, iters, outer, inner_iters, status, first, nvals, pad;
+    double rz, alpha, beta, bnorm, rnorm, target, bmean, scale, prev_rnorm, inner_target, shift;
+};
+
+struct SyncState {
+    unsigned count, gen;
+    int err, finished;
+};
+
+template <int MAXP>
+struct SolveParams {
+    int nprob, mixed, inner_tc, abs_tol, maxit, max_outer;
+    double tol, inner_tol;
+    long long timeout_ns;
+    SyncState *sync;
+    PState *st;
+    double *partials;   // [gridDim][MAXP][3]
+    int *sched;         // phase[MAXP], then offsets[MAXP + 1]
+    ProbDesc prob[MAXP];
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long sem_globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int phase_nvals(int ph)
+{
+    switch (ph) {
+        case PH_JACGS: return 1;
+        case PH_R0: return 3;
+        case PH_A: case PH_A32: return 1;
+        case PH_C: case PH_C32: case PH_R64: case PH_INIT32: return 2;
+        case PH_FINAL: return 1;
+        default: return 0;
+    }
+}
+
+__device__ __forceinline__ int64_t phase_items(const ProbDesc &P, int ph)
+{
+    switch (ph) {
+        case PH_JAC: case PH_UPD: case PH_FINAL: case PH_SHIFT:
+            return (P.nL + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS;
+        case PH_JACGS: case PH_R0: case PH_C: case PH_R64: case PH_INIT32: case PH_C32:
+            return (P.nG + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS;
+        case PH_AX0: case PH_A:
+            return (P.E + P.NE - 1) / P.NE;
+        case PH_A32:
+            return (P.E + P.NE32 - 1) / P.NE32;
+        default:
+            return 0;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Adds the block sum of v[0..2] into dst[0..2] (thread 0); all threads call.
+__device__ __forceinline__ void block_accumulate(double v[3], double *s_red, double *dst)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double s = warp_sum(v[k]);
+        if (lane == 0) s_red[warp * 3 + k] = s;
+        v[k] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < SEM_SOLVE_THREADS / 32; ++w) s += s_red[w * 3 + k];
+            dst[k] += s;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// element items
+// ---------------------------------------------------------------------------
+
+// kind 0: w64 = A64 x;  kind 1: FP64 p-update + w = A p + <p,w>;
+// kind 2: FP32 p32-update + w32 = A32 p32 + <p32,w32>.
+template <int NP, int KIND>
+__device__ __forceinline__ void elem_item(const ProbDesc &P, double beta, int first, int64_t g,
+                                          unsigned char *smem, double &acc)
+{
+    using C = AxCfg<NP>;
+    using T = typename std::conditional<KIND == 2, float, double>::type;
+    T *sm = reinterpret_cast<T *>(smem);
+    T *sD = sm, *sDT = sm + NP * NP;
+    const int grp = threadIdx.x / C::NP2;
+    const int tid = threadIdx.x - grp * C::NP2;
+    const bool inrange = grp < C::NE;
+    const int64_t e = g * C::NE + grp;
+    const bool active = inrange && e < P.E;
+    T *su = sm + 2 * NP * NP + (size_t)(inrange ? grp : 0) * 3 * C::NP3;
+    T *svr = su + C::NP3, *svs = svr + C::NP3;
+    const int64_t off = (active ? e : 0) * C::NP3;
+    const T *D = KIND == 2 ? (const T *)P.D32 : (const T *)P.D64;
+    const T *geo = (KIND == 2 ? (const T *)P.geo32 : (const T *)P.geo64) + (active ? e : 0) * 7 * C::NP3;
+    ax_load_D<NP, T>(D, sD, sDT);
+    if (KIND == 0) {
+        const double *x = P.x + off;
+        double *w = P.w + off;
+        auto load = [&](int q) { return (T)__ldcg(x + q); };
+        auto store = [&](int q, T v, T) { w[q] = v; };
+        ax_element<NP, T>(load, store, geo, (T)P.h1, (T)P.h2, sD, sDT, su, svr, svs, tid, active);
+    } else if (KIND == 1) {
+        const double *r = P.r + off, *mi = P.minv + off;
+        double *p = P.p + off, *w = P.w + off;
+        auto load = [&](int q) {
+            double pn = __ldcg(mi + q) * __ldcg(r + q);
+            if (!first) pn = fma(beta, __ldcg(p + q), pn);
+            p[q] = pn;
+            return (T)pn;
+        };
+        auto store = [&](int q, T v, T u) {
+            w[q] = v;
+            acc = fma((double)u, (double)v, acc);
+        };
+        ax_element<NP, T>(load, store, geo, (T)P.h1, (T)P.h2, sD, sDT, su, svr, svs, tid, active);
+    } else {
+        const float *r = P.r32 + off, *mi = P.minv32 + off;
+        float *p = P.p32 + off, *w = P.w32 + off;
+        const float b32 = (float)beta;
+        auto load = [&](int q) {
+            float pn = __ldcg(mi + q) * __ldcg(r + q);
+            if (!first) pn = fmaf(b32, __ldcg(p + q), pn);
+            p[q] = pn;
+            return (T)pn;
+        };
+        auto store = [&](int q, T v, T u) {
+            w[q] = v;
+            acc = fma((double)u, (double)v, acc);
+        };
+        ax_element<NP, T>(load, store, geo, (T)P.h1, (T)P.h2, sD, sDT, su, svr, svs, tid, active);
+    }
+}
+
+// TC inner operator (16-bit tensor-core contractions, FP32 vectors).
+template <int NP>
+__device__ __forceinline__ void elem_item_tc(const ProbDesc &P, double beta, int first, int64_t g,
+                                             int fp16, unsigned char *smem, double &acc)
+{
+    const float b32 = (float)beta;
+    auto load = [&](int64_t q) {
+        float pn = __ldcg(P.minv32 + q) * __ldcg(P.r32 + q);
+        if (!first) pn = fmaf(b32, __ldcg(P.p32 + q), pn);
+        P.p32[q] = pn;
+        return pn;
+    };
+    auto store = [&](int64_t q, float v, float u) {
+        P.w32[q] = v;
+        acc = fma((double)u, (double)v, acc);
+    };
+    ax_tc_group<NP>(load, store, P.geo32, P.D32, (float)P.h1, (float)P.h2, P.E, g, fp16, smem);
+}
+
+template <int NP>
+__device__ __forceinline__ void elem_dispatch_np(const ProbDesc &P, int ph, double beta, int first,
+                                                 int64_t g, int tc, unsigned char *smem, double &acc)
+{
+    if (ph == PH_AX0)
+        elem_item<NP, 0>(P, beta, first, g, smem, acc);
+    else if (ph == PH_A)
+        elem_item<NP, 1>(P, beta, first, g, smem, acc);
+    else if (tc)
+        elem_item_tc<NP>(P, beta, first, g, tc == 2, smem, acc);
+    else
+        elem_item<NP, 2>(P, beta, first, g, smem, acc);
+}
+
+template <int... NPs>
+struct ElemDispatch;
+
+template <>
+struct ElemDispatch<> {
+    __device__ static void run(const ProbDesc &, int, double, int, int64_t, int, unsigned char *,
+                               double &) {}
+};
+
+template <int NP0, int... NPs>
+struct ElemDispatch<NP0, NPs...> {
+    __device__ static void run(const ProbDesc &P, int ph, double beta, int first, int64_t g, int tc,
+                               unsigned char *smem, double &acc)
+    {
+        if (P.n == NP0)
+            elem_dispatch_np<NP0>(P, ph, beta, first, g, tc, smem, acc);
+        else
+            ElemDispatch<NPs...>::run(P, ph, beta, first, g, tc, smem, acc);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// unique-node and local-node items (one node per thread)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void uniq_item(const ProbDesc &P, const PState &S, int ph, int64_t chunk,
+                                          double v[3])
+{
+    const int64_t g = chunk * SEM_SOLVE_THREADS + threadIdx.x;
+    if (g >= P.nG) return;
+    int64_t idx[8];
+    const int m = gs_copies(P.gs, g, idx);
+    const int64_t f = idx[0];
+    switch (ph) {
+        case PH_JACGS: {
+            double s = 0.0;
+            for (int t = 0; t < m; ++t) s += __ldcg(P.minv + idx[t]);
+            const double rinv = 1.0 / s;
+            for (int t = 0; t < m; ++t) {
+                P.minv[idx[t]] = rinv;
+                if (P.minv32) P.minv32[idx[t]] = (float)rinv;
+            }
+            v[0] += __ldcg(P.b + f);
+        } break;
+        case PH_R0:
+        case PH_R64: {
+            double s = 0.0;
+            for (int t = 0; t < m; ++t) s += __ldcg(P.w + idx[t]);
+            const double bv = __ldcg(P.b + f) - S.bmean;
+            const double rv = bv - s;
+            for (int t = 0; t < m; ++t) P.r[idx[t]] = rv;
+            v[0] = fma(rv, rv, v[0]);
+            if (ph == PH_R0) {
+                v[1] = fma(rv, __ldcg(P.minv + f) * rv, v[1]);
+                v[2] = fma(bv, bv, v[2]);
+            } else {
+                v[1] = fma(bv, bv, v[1]);
+            }
+        } break;
+        case PH_C: {
+            double s = 0.0;
+            for (int t = 0; t < m; ++t) s += __ldcg(P.w + idx[t]);
+            const double pv = __ldcg(P.p + f);
+            const double rv = __ldcg(P.r + f) - S.alpha * s;
+            for (int t = 0; t < m; ++t) {
+                P.r[idx[t]] = rv;
+                P.x[idx[t]] = fma(S.alpha, pv, __ldcg(P.x + idx[t]));
+            }
+            v[0] = fma(rv, rv, v[0]);
+            v[1] = fma(rv, __ldcg(P.minv + f) * rv, v[1]);
+        } break;
+        case PH_INIT32: {
+            const float rv = (float)(__ldcg(P.r + f) / S.scale);
+            for (int t = 0; t < m; ++t) {
+                P.r32[idx[t]] = rv;
+                P.d32[idx[t]] = 0.0f;
+            }
+            const double rd = rv;
+            v[0] = fma(rd, rd, v[0]);
+            v[1] = fma(rd, (double)(__ldcg(P.minv32 + f) * rv), v[1]);
+        } break;
+        case PH_C32: {
+            float s = 0.0f;
+            for (int t = 0; t < m; ++t) s += __ldcg(P.w32 + idx[t]);
+            const float a = (float)S.alpha;
+            const float pv = __ldcg(P.p32 + f);
+            const float rv = __ldcg(P.r32 + f) - a * s;
+            const float dv = fmaf(a, pv, __ldcg(P.d32 + f));
+            for (int t = 0; t < m; ++t) {
+                P.r32[idx[t]] = rv;
+                P.d32[idx[t]] = dv;
+            }
+            const double rd = rv;
+            v[0] = fma(rd, rd, v[0]);
+            v[1] = fma(rd, (double)(__ldcg(P.minv32 + f) * rv), v[1]);
+        } break;
+        default: break;
+    }
+}
+
+__device__ __forceinline__ void local_item(const ProbDesc &P, const PState &S, int ph, int64_t chunk,
+                                           double v[3])
+{
+    const int64_t q = chunk * SEM_SOLVE_THREADS + threadIdx.x;
+    if (q >= P.nL) return;
+    const int n = P.n, n3 = n * n * n;
+    const int64_t e = q / n3;
+    const int l = (int)(q - e * n3);
+    switch (ph) {
+        case PH_JAC: {
+            const int i = l % n, j = (l / n) % n, k = l / (n * n);
+            const double *g = P.geo64 + e * 7 * n3;
+            const double *D = P.D64;
+            double s = 0.0;
+            for (int t = 0; t < n; ++t) {
+                const double a = D[t * n + i], b = D[t * n + j], c = D[t * n + k];
+                s += a * a * g[0 * n3 + (k * n + j) * n + t];
+                s += b * b * g[1 * n3 + (k * n + t) * n + i];
+                s += c * c * g[2 * n3 + (t * n + j) * n + i];
+            }
+            const double di = D[i * n + i], dj = D[j * n + j], dk = D[k * n + k];
+            s += 2.0 * (di * dj * g[3 * n3 + l] + di * dk * g[4 * n3 + l] + dj * dk * g[5 * n3 + l]);
+            P.minv[q] = P.h1 * s + P.h2 * g[6 * n3 + l];
+        } break;
+        case PH_UPD:
+            P.x[q] = fma(S.scale, (double)__ldcg(P.d32 + q), __ldcg(P.x + q));
+            break;
+        case PH_FINAL:
+            v[0] = fma(P.geo64[(e * 7 + 6) * n3 + l], __ldcg(P.x + q), v[0]);
+            break;
+        case PH_SHIFT:
+            P.x[q] = __ldcg(P.x + q) - S.shift;
+            break;
+        default: break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-problem state machine (run by one thread of the last CTA of a step)
+// ---------------------------------------------------------------------------
+
+template <int MAXP>
+__device__ void advance(const SolveParams<MAXP> &prm, const ProbDesc &P, PState &S, const double *red)
+{
+    const int ph = S.phase;
+    auto finish = [&](int status) {
+        S.status = status;
+        S.phase = P.singular ? PH_FINAL : PH_DONE;
+    };
+    switch (ph) {
+        case PH_JAC: S.phase = PH_JACGS; break;
+        case PH_JACGS:
+            S.bmean = P.singular ? red[0] / (double)P.nG : 0.0;
+            S.phase = PH_AX0;
+            break;
+        case PH_AX0: S.phase = prm.mixed ? PH_R64 : PH_R0; break;
+        case PH_R0: {
+            S.bnorm = sqrt(red[2]);
+            S.rnorm = sqrt(red[0]);
+            S.target = prm.abs_tol ? prm.tol : prm.tol * S.bnorm;
+            if (!isfinite(S.rnorm) || !isfinite(S.bnorm)) { finish(SEM_ERR_BREAKDOWN); break; }
+            if (S.rnorm <= S.target) { finish(SEM_OK); break; }
+            if (prm.maxit <= 0) { finish(SEM_ERR_NOT_CONVERGED); break; }
+            S.rz = red[1];
+            S.first = 1;
+            S.beta = 0.0;
+            S.phase = PH_A;
+        } break;
+        case PH_A: {
+            const double pw = red[0];
+            if (!(pw > 0.0) || !isfinite(pw)) { finish(SEM_ERR_BREAKDOWN); break; }
+            S.alpha = S.rz / pw;
+            S.phase = PH_C;
+        } break;
+        case PH_C: {
+            S.iters += 1;
+            S.rnorm = sqrt(red[0]);
+            if (!isfinite(S.rnorm)) { finish(SEM_ERR_BREAKDOWN); break; }
+            if (S.rnorm <= S.target) { finish(SEM_OK); break; }
+            if (S.iters >= prm.maxit) { finish(SEM_ERR_NOT_CONVERGED); break; }
+            S.beta = red[1] / S.rz;
+            S.rz = red[1];
+            S.first = 0;
+            S.phase = PH_A;
+        } break;
+        case PH_R64: {
+            const double rn = sqrt(red[0]);
+            if (S.outer == 0) {
+                S.bnorm = sqrt(red[1]);
+                S.target = prm.abs_tol ? prm.tol : prm.tol * S.bnorm;
+            }
+            S.rnorm = rn;
+            if (!isfinite(rn) || !isfinite(S.bnorm)) { finish(SEM_ERR_BREAKDOWN); break; }
+            if (rn <= S.target) { finish(SEM_OK); break; }
+            if (S.outer >= prm.max_outer || S.iters >= prm.maxit) { finish(SEM_ERR_NOT_CONVERGED); break; }
+            if (S.outer > 0 && rn > 0.5 * S.prev_rnorm) { finish(SEM_ERR_NOT_CONVERGED); break; }
+            S.prev_rnorm = rn;
+            S.scale = rn;
+            S.phase = PH_INIT32;
+        } break;
+        case PH_INIT32:
+            S.inner_target = prm.inner_tol * sqrt(red[0]);
+            S.rz = red[1];
+            S.first = 1;
+            S.beta = 0.0;
+            S.inner_iters = 0;
+            S.phase = (red[0] > 0.0) ? PH_A32 : PH_UPD;
+            break;
+        case PH_A32: {
+            const double pw = red[0];
+            if (!(pw > 0.0) || !isfinite(pw)) { S.phase = PH_UPD; break; }
+            S.alpha = S.rz / pw;
+            S.phase = PH_C32;
+        } break;
+        case PH_C32: {
+            S.iters += 1;
+            S.inner_iters += 1;
+            const double rn = sqrt(red[0]);
+            if (!isfinite(rn) || rn <= S.inner_target || S.iters >= prm.maxit) { S.phase = PH_UPD; break; }
+            S.beta = red[1] / S.rz;
+            S.rz = red[1];
+            S.first = 0;
+            S.phase = PH_A32;
+        } break;
+        case PH_UPD: S.outer += 1; S.phase = PH_AX0; break;
+        case PH_FINAL: S.shift = red[0] / P.volume; S.phase = PH_SHIFT; break;
+        case PH_SHIFT: S.phase = PH_DONE; break;
+        default: S.phase = PH_DONE; break;
+    }
+    S.nvals = phase_nvals(S.phase);
+}
+
+// ---------------------------------------------------------------------------
+// the persistent kernel
+// ---------------------------------------------------------------------------
+
+template <int MAXP, int... NPs>
+__global__ void __launch_bounds__(SEM_SOLVE_THREADS, 2)
+    k_solve(const __grid_constant__ SolveParams<MAXP> prm)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_part[MAXP][3];
+    __shared__ double s_red[SEM_SOLVE_THREADS / 32 * 3];
+    __shared__ int s_phase[MAXP];
+    __shared__ long long s_offs[MAXP + 1];
+    __shared__ double s_alpha[MAXP], s_beta[MAXP], s_bmean[MAXP], s_scale[MAXP], s_shift[MAXP];
+    __shared__ int s_first[MAXP];
+    __shared__ int s_last, s_stop;
+    __shared__ unsigned s_gen;
+    const int np = prm.nprob;
+    SyncState *sync = prm.sync;
+
+    for (int step = 0;; ++step) {
+        // ---- schedule of this step
+        if (threadIdx.x == 0) {
+            long long o = 0;
+            for (int p = 0; p < np; ++p) {
+                int ph;
+                if (step == 0) {
+                    ph = PH_JAC;
+                } else {
+                    ph = ((volatile int *)prm.sched)[p];
+                }
+                s_phase[p] = ph;
+                s_offs[p] = o;
+                o += phase_items(prm.prob[p], ph);
+            }
+            s_offs[np] = o;
+            s_stop = (step > 0 && ((volatile int *)&sync->finished)[0]) ||
+                     ((volatile int *)&sync->err)[0];
+        }
+        for (int p = threadIdx.x; p < np; p += blockDim.x) {
+            const volatile PState *S = prm.st + p;
+            s_alpha[p] = S->alpha;
+            s_beta[p] = S->beta;
+            s_bmean[p] = S->bmean;
+            s_scale[p] = S->scale;
+            s_shift[p] = S->shift;
+            s_first[p] = S->first;
+            s_part[p][0] = s_part[p][1] = s_part[p][2] = 0.0;
+        }
+        __syncthreads();
+        if (s_stop) break;
+
+        // ---- work items
+        const long long total = s_offs[np];
+        double v[3] = {0.0, 0.0, 0.0};
+        double acc = 0.0;
+        int cur = -1;
+        for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+            int p = 0;
+            while (p + 1 < np && s_offs[p + 1] <= it) ++p;
+            if (p != cur) {
+                if (cur >= 0) {
+                    v[0] += acc;
+                    acc = 0.0;
+                    block_accumulate(v, s_red, s_part[cur]);
+                }
+                cur = p;
+            }
+            const ProbDesc &P = prm.prob[p];
+            const int ph = s_phase[p];
+            const int64_t local = it - s_offs[p];
+            PState S;
+            S.alpha = s_alpha[p];
+            S.beta = s_beta[p];
+            S.bmean = s_bmean[p];
+            S.scale = s_scale[p];
+            S.shift = s_shift[p];
+            if (ph == PH_AX0 || ph == PH_A || ph == PH_A32) {
+                ElemDispatch<NPs...>::run(P, ph, S.beta, s_first[p], local, prm.inner_tc, smem, acc);
+            } else if (ph == PH_JAC || ph == PH_UPD || ph == PH_FINAL || ph == PH_SHIFT) {
+                local_item(P, S, ph, local, v);
+            } else {
+                uniq_item(P, S, ph, local, v);
+            }
+        }
+        if (cur >= 0) {
+            v[0] += acc;
+            block_accumulate(v, s_red, s_part[cur]);
+        }
+
+        // ---- publish partials, reducing barrier
+        double *part = prm.partials + (size_t)blockIdx.x * MAXP * 3;
+        for (int t = threadIdx.x; t < np * 3; t += blockDim.x) part[t] = s_part[t / 3][t % 3];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_gen = ((volatile unsigned *)&sync->gen)[0];
+            const unsigned arrived = atomicAdd(&sync->count, 1u);
+            s_last = (arrived == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            // fixed-order reduction of every (problem, value) pair: one warp each
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            for (int pk = warp; pk < np * 3; pk += SEM_SOLVE_THREADS / 32) {
+                const int p = pk / 3, k = pk % 3;
+                double s = 0.0;
+                if (k < phase_nvals(s_phase[p]))
+                    for (int b = lane; b < (int)gridDim.x; b += 32)
+                        s += __ldcg(prm.partials + ((size_t)b * MAXP + p) * 3 + k);
+                s = warp_sum(s);
+                if (lane == 0) s_part[p][k] = s;
+            }
+            __syncthreads();
+            for (int p = threadIdx.x; p < np; p += blockDim.x) {
+                PState S = prm.st[p];
+                S.phase = s_phase[p];
+                advance<MAXP>(prm, prm.prob[p], S, s_part[p]);
+                prm.st[p] = S;
+                prm.sched[p] = S.phase;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int fin = 1;
+                for (int p = 0; p < np; ++p) fin &= (prm.sched[p] == PH_DONE);
+                sync->finished = fin;
+                sync->count = 0;
+                __threadfence();
+                atomicAdd(&sync->gen, 1u);
+            }
+        } else if (threadIdx.x == 0) {
+            const unsigned long long t0 = sem_globaltimer();
+            while (ld_acquire_u32(&sync->gen) == s_gen) {
+                if (((volatile int *)&sync->err)[0]) break;
+                if ((long long)(sem_globaltimer() - t0) > prm.timeout_ns) {
+                    atomicExch(&sync->err, SEM_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(128);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+    }
+}
+
+// Dynamic shared memory of the element phases of one problem order.
+template <int NP>
+constexpr size_t solve_smem_np()
+{
+    return ax_smem_bytes<NP, double>() > ax_tc_smem_bytes<NP>() ? ax_smem_bytes<NP, double>()
+                                                                 : ax_tc_smem_bytes<NP>();
+}
+
+template <int... NPs>
+struct SmemMax;
+template <>
+struct SmemMax<> {
+    static constexpr size_t v = 0;
+};
+template <int NP0, int... NPs>
+struct SmemMax<NP0, NPs...> {
+    static constexpr size_t v = solve_smem_np<NP0>() > SmemMax<NPs...>::v ? solve_smem_np<NP0>()
+                                                                          : SmemMax<NPs...>::v;
+};
+
+// Host launcher (cooperative, grid sized for co-residency).
+template <int MAXP, int... NPs>
+int launch_solve(const SolveParams<MAXP> &prm, int num_sms, long long max_items, cudaStream_t s)
+{
+    auto kern = k_solve<MAXP, NPs...>;
+    const size_t smem = SmemMax<NPs...>::v;
+    static bool attr = false;
+    if (!attr) {
+        SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    int per_sm = 0;
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SEM_SOLVE_THREADS, smem));
+    if (per_sm < 1) return SEM_ERR_ARG;
+    long long grid = (long long)per_sm * num_sms;
+    if (grid > max_items) grid = max_items;
+    if (grid < 1) grid = 1;
+    void *args[] = {(void *)&prm};
+    SEM_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)grid),
+                                         dim3(SEM_SOLVE_THREADS), args, smem, s));
+    return SEM_OK;
+}
+
+// Maximum grid the solver may use (sizes the partials buffer).
+#define SEM_SOLVE_MAX_GRID_PER_SM 8

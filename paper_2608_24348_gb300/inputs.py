@@ -131,13 +131,11 @@ def eval_fourier(K, cc, cs, x, y, z, chunk=1 << 16):
     if is_torch:
         import torch
         dev = x.device
-        Kt = torch.as_tensor(K, device=dev)
-        cct = torch.as_tensor(cc, device=dev, dtype=torch.float64)
-        cst = torch.as_tensor(cs, device=dev, dtype=torch.float64)
-        out = torch.empty_like(x, dtype=torch.float64)
+        out = torch.empty(x.numel(), dtype=torch.float64, device=dev)
         n = x.numel()
-        for s in range(0, n, chunk * 16):
-            sl = slice(s, min(n, s + chunk * 16))
+        step = 1 << 22
+        for s in range(0, n, step):
+            sl = slice(s, min(n, s + step))
             tabs = []
             for c in (x, y, z):
                 e = torch.exp(1j * c.reshape(-1)[sl].to(torch.float64))
@@ -146,10 +144,12 @@ def eval_fourier(K, cc, cs, x, y, z, chunk=1 << 16):
                     pw[kmax + p] = pw[kmax + p - 1] * e
                     pw[kmax - p] = pw[kmax - p + 1] * e.conj()
                 tabs.append(pw)
-            zsum = (tabs[0][Kt[:, 0] + kmax] * tabs[1][Kt[:, 1] + kmax] * tabs[2][Kt[:, 2] + kmax])
-            val = (cct[:, None] * zsum.real + cst[:, None] * zsum.imag).sum(0)
-            out.reshape(-1)[sl] = val
-        return out
+            acc = torch.zeros(e.numel(), dtype=torch.float64, device=dev)
+            for m in range(K.shape[0]):
+                zz = tabs[0][K[m, 0] + kmax] * tabs[1][K[m, 1] + kmax] * tabs[2][K[m, 2] + kmax]
+                acc += float(cc[m]) * zz.real + float(cs[m]) * zz.imag
+            out[sl] = acc
+        return out.reshape(x.shape)
     x = np.asarray(x, dtype=np.float64).reshape(-1)
     y = np.asarray(y, dtype=np.float64).reshape(-1)
     z = np.asarray(z, dtype=np.float64).reshape(-1)

@@ -41,7 +41,7 @@ class CtxInfo(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("abs_tol", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("inner", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("max_outer", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("wait_timeout_s", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -138,11 +138,12 @@ def stream_ptr(stream=None):
     return stream.cuda_stream
 
 
-def opts(tol=1e-10, abs_tol=False, maxit=20000, inner="f64", inner_tol=1e-4, max_outer=50):
+def opts(tol=1e-10, abs_tol=False, maxit=20000, inner="f64", inner_tol=1e-4, max_outer=50,
+         wait_timeout_s=0.0):
     o = SolveOpts()
     o.tol, o.abs_tol, o.maxit = tol, int(abs_tol), maxit
     o.inner = DTYPES[inner] if isinstance(inner, str) else int(inner)
-    o.inner_tol, o.max_outer = inner_tol, max_outer
+    o.inner_tol, o.max_outer, o.wait_timeout_s = inner_tol, max_outer, wait_timeout_s
     return o
 
 

@@ -74,6 +74,33 @@ def test_ax_f64_f32(sem, N, nel, perturb, h1, h2):
     assert rel_err(wd32.cpu().numpy().astype(np.float64), ref32) <= 1e-5
 
 
+@pytest.mark.parametrize("dtype,bound", [("bf16_tc", 3e-2), ("f16_tc", 4e-3)])
+@pytest.mark.parametrize("N,nel,perturb", [(1, (3, 2, 2), 0.1), (3, (3, 2, 5), 0.1),
+                                           (5, (4, 4, 4), 0.1), (7, (3, 5, 2), 0.1),
+                                           (9, (2, 2, 3), 0.1)])
+def test_ax_tensor_core(sem, dtype, bound, N, nel, perturb):
+    """16-bit tensor-core contractions: error of the order of the 16-bit rounding
+    (no FP64-level bar), measured on a continuous field."""
+    torch, dev = torch_dev()
+    ctx, m, _ = make(sem, N, nel, perturb)
+    u = inputs.unique_uniform_field(N, nel, seed=inputs.SEED_FIELD).astype(np.float32)
+    for h1, h2 in ((1.0, 0.0), (0.01, 1000.0)):
+        ref = m.ax(u.astype(np.float64), h1, h2)
+        ud = torch.from_numpy(u).to(dev)
+        wd = torch.empty_like(ud)
+        ctx.ax(ud, wd, h1, h2, dtype)
+        err = rel_err(wd.cpu().numpy().astype(np.float64), ref)
+        assert err <= bound, (dtype, N, h1, h2, err)
+
+
+def test_ax_tensor_core_rejects_high_order(sem):
+    torch, dev = torch_dev()
+    ctx, m, _ = make(sem, 11, (1, 1, 1), 0.0)
+    u = torch.zeros(ctx.nL, dtype=torch.float32, device=dev)
+    with pytest.raises(sem.SemError):
+        ctx.ax(u, torch.empty_like(u), 1.0, 0.0, "bf16_tc")
+
+
 def test_ax_host_pointers(sem):
     """Host (numpy) buffers go through the library's staging path."""
     ctx, m, _ = make(sem, 4, (3, 3, 2), 0.1)

@@ -1,0 +1,146 @@
+"""GPU parity of the persistent Jacobi-PCG and the FP64 iterative refinement.
+
+Bars (FP64 solves against the oracle solved to a tighter 1e-12): relative
+solution difference <= 1e-9; the oracle's FP64 residual of the GPU solution
+<= 1.5 x the requested tolerance; FP64 iteration counts within 2 of the
+oracle's.  Mixed precision (FP32 / BF16-TC / FP16-TC inner) must reach the
+same FP64 residual and solution bars.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import fourier_rhs, pair, rel, sine_rhs, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+F64_CASES = [
+    # N, nel, perturb, h2, periodic
+    (5, (4, 4, 4), 0.0, 0.0, (1, 1, 1)),   # the plain FP64 Poisson workload
+    (3, (3, 2, 3), 0.15, 0.0, (1, 1, 1)),
+    (1, (4, 3, 2), 0.1, 0.0, (1, 1, 1)),
+    (9, (2, 2, 2), 0.1, 0.0, (1, 1, 1)),
+    (7, (3, 3, 2), 0.1, 2.0, (1, 1, 1)),   # Helmholtz
+    (4, (3, 2, 2), 0.0, 0.0, (1, 0, 1)),   # Neumann in y
+    (15, (1, 1, 2), 0.0, 0.5, (1, 1, 1)),
+]
+
+
+@pytest.mark.parametrize("N,nel,perturb,h2,periodic", F64_CASES)
+def test_pcg_f64_matches_oracle(sem, N, nel, perturb, h2, periodic):
+    torch, dev = torch_dev()
+    ctx, m, _ = pair(sem, N, nel, perturb, periodic)
+    bg, bo, _ = sine_rhs(ctx, m, (1, 2, 1))
+    x = torch.zeros_like(bg)
+    info = ctx.pcg_solve(bg, x, 1.0, h2, tol=1e-10)
+    assert info["status"] == 0, info
+    xr, ir = m.pcg(bo, 1.0, h2, tol=1e-10)
+    assert ir["status"] == 0
+    assert abs(info["iters"] - ir["iters"]) <= 2, (info, ir)
+    xg = x.cpu().numpy()
+    r, bn = m.residual(bo, xg, 1.0, h2)
+    assert r <= 1.5e-10 * bn, (r, bn)
+    xt, it = m.pcg(bo, 1.0, h2, tol=1e-12)
+    assert rel(xg, xt) <= 1e-9
+
+
+@pytest.mark.parametrize("inner,inner_tol", [("f32", 1e-4), ("bf16_tc", 1e-2), ("f16_tc", 1e-2)])
+@pytest.mark.parametrize("N,nel,perturb", [(7, (3, 3, 3), 0.1), (5, (4, 3, 2), 0.1)])
+def test_pcg_mixed_refinement(sem, inner, inner_tol, N, nel, perturb):
+    torch, dev = torch_dev()
+    ctx, m, _ = pair(sem, N, nel, perturb)
+    bg, bo = fourier_rhs(ctx, m)
+    x = torch.zeros_like(bg)
+    info = ctx.pcg_solve(bg, x, 1.0, 0.0, tol=1e-10, inner=inner, inner_tol=inner_tol)
+    assert info["status"] == 0, info
+    assert info["outer_iters"] >= 1
+    xg = x.cpu().numpy()
+    r, bn = m.residual(bo, xg, 1.0, 0.0)
+    assert r <= 1.5e-10 * bn, (r, bn, info)
+    xt, _ = m.pcg(bo, 1.0, 0.0, tol=1e-12)
+    assert rel(xg, xt) <= 1e-9
+
+
+def test_pcg_helmholtz_mixed(sem):
+    torch, dev = torch_dev()
+    ctx, m, _ = pair(sem, 7, (3, 2, 3), 0.1)
+    bg, bo, _ = sine_rhs(ctx, m, (2, 1, 1))
+    x = torch.zeros_like(bg)
+    h1, h2 = 1.0 / 1600, 11.0 / 6.0 / 1e-3
+    info = ctx.pcg_solve(bg, x, h1, h2, tol=1e-10, inner="f32")
+    assert info["status"] == 0, info
+    r, bn = m.residual(bo, x.cpu().numpy(), h1, h2)
+    assert r <= 1.5e-10 * bn
+
+
+def test_pcg_status_codes(sem):
+    torch, dev = torch_dev()
+    ctx, m, _ = pair(sem, 4, (3, 3, 3), 0.1)
+    bg, bo, _ = sine_rhs(ctx, m)
+    x = torch.zeros_like(bg)
+    info = ctx.pcg_solve(bg, x, tol=1e-14, maxit=3)
+    assert info["status"] == sem.ERR_NOT_CONVERGED and info["iters"] == 3
+    bad = bg.clone()
+    bad[7] = float("nan")
+    x.zero_()
+    assert ctx.pcg_solve(bad, x, tol=1e-10)["status"] == sem.ERR_BREAKDOWN
+    x.zero_()
+    info = ctx.pcg_solve(torch.zeros_like(bg), x, tol=1e-10)
+    assert info["status"] == 0 and info["iters"] == 0 and float(x.abs().max()) == 0.0
+
+
+def test_pcg_wait_timeout_then_context_still_usable(sem):
+    """A solver wait that runs out ends the solve with SEM_ERR_TIMEOUT (no trap);
+    the next solve on the same context succeeds."""
+    torch, dev = torch_dev()
+    ctx, m, _ = pair(sem, 7, (4, 4, 4), 0.0)
+    bg, bo, _ = sine_rhs(ctx, m)
+    x = torch.zeros_like(bg)
+    info = ctx.pcg_solve(bg, x, tol=1e-10, wait_timeout_s=1e-9)
+    assert info["status"] == sem.ERR_TIMEOUT, info
+    x.zero_()
+    info = ctx.pcg_solve(bg, x, tol=1e-10)
+    assert info["status"] == 0
+    r, bn = m.residual(bo, x.cpu().numpy(), 1.0, 0.0)
+    assert r <= 1.5e-10 * bn
+
+
+def test_pcg_host_buffers(sem):
+    ctx, m, _ = pair(sem, 5, (2, 3, 2), 0.1)
+    bg, bo, _ = sine_rhs(ctx, m)
+    b = bg.cpu().numpy().copy()
+    x = np.zeros_like(b)
+    info = ctx.pcg_solve(b, x, tol=1e-10)
+    assert info["status"] == 0
+    r, bn = m.residual(bo, x, 1.0, 0.0)
+    assert r <= 1.5e-10 * bn
+
+
+def test_pcg_nonzero_initial_guess(sem):
+    torch, dev = torch_dev()
+    ctx, m, _ = pair(sem, 6, (2, 2, 3), 0.1)
+    bg, bo, us = sine_rhs(ctx, m)
+    x0 = torch.from_numpy(0.9 * us).to(dev)
+    info = ctx.pcg_solve(bg, x0, tol=1e-10)
+    xr, ir = m.pcg(bo, x0=0.9 * us, tol=1e-10)
+    assert info["status"] == 0 and abs(info["iters"] - ir["iters"]) <= 2
+    assert rel(x0.cpu().numpy(), xr) <= 1e-9
+
+
+def test_pcg_full_size_pressure_poisson(sem):
+    """32^3 elements, N=7, deformed; RHS = div of a random smooth field (|k| <= 8).
+    FP64 PCG and FP32-inner refinement both reach the FP64 relative residual
+    1e-10, checked by the oracle's FP64 operator on the whole mesh."""
+    torch, dev = torch_dev()
+    ctx, m, _ = pair(sem, 7, (32, 32, 32), 0.1)
+    bg, bo = fourier_rhs(ctx, m)
+    x64 = torch.zeros_like(bg)
+    i64 = ctx.pcg_solve(bg, x64, tol=1e-10)
+    assert i64["status"] == 0, i64
+    xm = torch.zeros_like(bg)
+    im = ctx.pcg_solve(bg, xm, tol=1e-10, inner="f32", inner_tol=1e-4)
+    assert im["status"] == 0, im
+    for x in (x64, xm):
+        r, bn = m.residual(bo, x.cpu().numpy(), 1.0, 0.0)
+        assert r <= 1.5e-10 * bn, (r, bn)
+    assert rel(xm.cpu().numpy(), x64.cpu().numpy()) <= 1e-9
