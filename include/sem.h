@@ -54,6 +54,7 @@ extern "C" {
 #define SEM_ERR_NOT_CONVERGED (-5) /* maxit reached; x holds the last iterate */
 #define SEM_ERR_BREAKDOWN (-6)     /* <p,Ap> <= 0 or a non-finite residual */
 #define SEM_ERR_TIMEOUT (-7)       /* a bounded device-side wait gave up */
+#define SEM_ERR_TOO_LARGE (-8)     /* problem larger than a fixed-size scratch area */
 
 typedef enum {
     SEM_F64 = 0,     /* FP64 storage and arithmetic */
@@ -185,6 +186,35 @@ SEM_API int sem_last_solve_info(sem_ctx *ctx, sem_solve_info *info);
 SEM_API int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const double *const *b,
                           double *const *x, const double *h1, const double *h2,
                           const sem_solve_opts *opts, sem_solve_info *infos, void *stream);
+
+/* Largest problem (local nodes E (N+1)^3) that sem_pcg_solve_noalloc accepts. */
+#define SEM_NOALLOC_MAX_NODES 1000000
+
+/* FP64 Jacobi-PCG that allocates nothing -- an addition of this library; the
+ * paper has no counterpart.  It is meant for callers that cannot call
+ * cudaMalloc: code running while a stream is captured into a CUDA graph, code
+ * whose device memory is owned by another allocator (a framework's caching
+ * allocator, a plugin host, a service with a fixed memory plan), and code that
+ * must avoid cudaMalloc's implicit device synchronisation.  It needs no
+ * context: the caller passes the mesh shape (N, nelx, nely, nelz, periodic),
+ * the geometric factors geom as a device FP64 array laid out element by
+ * element, [E][7][(N+1)^3] with components G11 G22 G33 G12 G13 G23 B (the
+ * factors sem_geom exports, regrouped per element), the assembled RHS b and
+ * the initial guess / solution x (device FP64 E-vectors), and host opts/info
+ * (info is required; opts->inner must be SEM_F64).  The arithmetic is that of
+ * sem_pcg_solve (same persistent kernel).  Every scratch vector, partial sum
+ * and the solver state live in one file-scope device array of fixed size
+ * (about 33 MB, held on every GPU that loads the library until the process
+ * exits), so problems with more than SEM_NOALLOC_MAX_NODES local nodes return
+ * SEM_ERR_TOO_LARGE.  The first call on a device looks up that array's device
+ * address (once per device); make that first call before any stream capture
+ * begins.  All calls share the one array: calls that overlap on the GPU (from
+ * several streams or host threads) race and give wrong results.  The call
+ * synchronises the stream and returns info->status. */
+SEM_API int sem_pcg_solve_noalloc(int N, int nelx, int nely, int nelz, const int periodic[3],
+                                  const double *geom, const double *b, double *x, double h1,
+                                  double h2, const sem_solve_opts *opts, sem_solve_info *info,
+                                  void *stream);
 
 /* ---- Taylor-Green vortex stepper (Sec. 3) ---- */
 

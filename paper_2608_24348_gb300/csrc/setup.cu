@@ -32,6 +32,7 @@ extern "C" const char *sem_strerror(int code)
         case SEM_ERR_NOT_CONVERGED: return "solver did not converge";
         case SEM_ERR_BREAKDOWN: return "solver breakdown";
         case SEM_ERR_TIMEOUT: return "device-side wait timed out";
+        case SEM_ERR_TOO_LARGE: return "problem exceeds the fixed scratch size";
         default: return "unknown error";
     }
 }

@@ -19,6 +19,8 @@ DTYPES = {"f64": F64, "f32": F32, "bf16_tc": BF16_TC, "f16_tc": F16_TC}
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_BAD_MESH, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT = \
     0, -1, -2, -3, -4, -5, -6, -7
+ERR_TOO_LARGE = -8
+NOALLOC_MAX_NODES = 1000000
 
 _lib = None
 _lock = threading.Lock()
@@ -61,7 +63,8 @@ class TgvDiag(ctypes.Structure):
 EXPORTS = ["sem_setup", "sem_destroy", "sem_get_info", "sem_strerror", "sem_coords", "sem_geom",
            "sem_ax", "sem_dssum", "sem_jacobi", "sem_solve_opts_default", "sem_pcg_solve",
            "sem_last_solve_info", "sem_pcg_solve_batched", "sem_tgv_init", "sem_tgv_set",
-           "sem_tgv_step", "sem_tgv_get", "sem_tgv_energy", "sem_tgv_destroy"]
+           "sem_tgv_step", "sem_tgv_get", "sem_tgv_energy", "sem_tgv_destroy",
+           "sem_pcg_solve_noalloc"]
 
 
 def lib_path() -> str:
@@ -108,6 +111,10 @@ def load(build_if_missing: bool = True):
         L.sem_tgv_energy.argtypes = [vp, dp, dp, vp]
         L.sem_tgv_destroy.argtypes = [vp]
         L.sem_tgv_destroy.restype = None
+        L.sem_pcg_solve_noalloc.argtypes = [ctypes.c_int] * 4 + [ip, vp, vp, vp, ctypes.c_double,
+                                                                 ctypes.c_double,
+                                                                 ctypes.POINTER(SolveOpts),
+                                                                 ctypes.POINTER(SolveInfo), vp]
         _lib = L
         return L
 
@@ -257,6 +264,23 @@ def pcg_solve_batched(ctxs, bs, xs, h1s, h2s, sync=True, stream=None, **kw):
     if rc not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT):
         _check(rc, "sem_pcg_solve_batched")
     return [infos[i].as_dict() for i in range(n)]
+
+
+def pcg_solve_noalloc(N, nel, periodic, geom, b, x, h1=1.0, h2=0.0, stream=None, **kw):
+    """FP64 PCG without any allocation (scratch in a fixed static device array).
+
+    geom: device FP64 tensor [E][7][(N+1)^3]; b, x: device FP64 E-vectors.
+    Synchronous; returns the info dict (raises on argument / CUDA errors)."""
+    L = load()
+    o = opts(**kw)
+    info = SolveInfo()
+    per = (ctypes.c_int * 3)(*[int(bool(p)) for p in periodic])
+    rc = L.sem_pcg_solve_noalloc(int(N), int(nel[0]), int(nel[1]), int(nel[2]), per, ptr(geom),
+                                 ptr(b), ptr(x), float(h1), float(h2), ctypes.byref(o),
+                                 ctypes.byref(info), _sp(b, stream))
+    if rc not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT):
+        _check(rc, "sem_pcg_solve_noalloc")
+    return info.as_dict()
 
 
 class TGV:

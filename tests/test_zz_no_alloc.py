@@ -1,0 +1,43 @@
+"""sem_pcg_solve_noalloc: the PCG entry point for callers that cannot allocate
+device memory (inside a stream capture, under another allocator's fixed
+budget).  It must agree with sem_pcg_solve, call after call, while its
+scratch lives in one fixed static device array.  This file sorts last so that
+a stop-at-first-failure run has already run every other test."""
+import pytest
+
+from helpers import pair, rel, sine_rhs, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _geom_per_element(ctx):
+    torch, dev = torch_dev()
+    n3 = (ctx.N + 1) ** 3
+    g = torch.empty(7 * ctx.nL, dtype=torch.float64, device=dev)
+    ctx.geom(g)
+    return g.view(7, ctx.E, n3).permute(1, 0, 2).contiguous()
+
+
+@pytest.mark.parametrize("N,nel,perturb,h2", [(5, (4, 4, 4), 0.1, 0.0), (7, (3, 2, 3), 0.1, 1.5)])
+def test_noalloc_matches_pcg_on_two_calls_in_a_row(sem, N, nel, perturb, h2):
+    torch, dev = torch_dev()
+    ctx, _, _ = pair(sem, N, nel, perturb, with_oracle=False)
+    bg, _, _ = sine_rhs(ctx, None, (1, 2, 1))
+    xref = torch.zeros_like(bg)
+    iref = ctx.pcg_solve(bg, xref, 1.0, h2, tol=1e-10)
+    assert iref["status"] == 0
+    geom = _geom_per_element(ctx)
+    for _ in range(2):
+        x = torch.zeros_like(bg)
+        info = sem.pcg_solve_noalloc(N, nel, (1, 1, 1), geom, bg, x, 1.0, h2, tol=1e-10)
+        assert info["status"] == 0, info
+        assert info["iters"] == iref["iters"]
+        assert rel(x.cpu().numpy(), xref.cpu().numpy()) <= 1e-9
+
+
+def test_noalloc_rejects_problems_beyond_its_scratch(sem):
+    torch, dev = torch_dev()
+    small = torch.zeros(8, dtype=torch.float64, device=dev)
+    with pytest.raises(sem.SemError) as e:
+        sem.pcg_solve_noalloc(7, (20, 20, 20), (1, 1, 1), small, small, small, 1.0, 0.0)
+    assert e.value.code == sem.ERR_TOO_LARGE
