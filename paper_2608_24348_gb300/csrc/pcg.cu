@@ -1,4 +1,5 @@
 // pcg.cu -- host side of the persistent PCG / iterative-refinement solver.
+#include <stddef.h>
 #include <string.h>
 
 #include <vector>
@@ -182,6 +183,33 @@ int sem_pcg_solve_dev(sem_ctx *c, int slot, const double *b, double *x, double h
     ProbDesc d;
     fill_desc(c, c->ws[slot], b, x, h1, h2, mixed, tc, d);
     return enqueue(c, o, &d, 1, s);
+}
+
+// Several device-pointer solves on one context (workspace slots 0..np-1) in one launch.
+int sem_pcg_solve_dev_batch(sem_ctx *c, int np, const double *const *b, double *const *x, double h1,
+                            double h2, const sem_solve_opts &o, cudaStream_t s)
+{
+    if (np < 1 || np > 8 || np > c->nws) return SEM_ERR_ARG;
+    const bool mixed = o.inner != SEM_F64;
+    const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC;
+    if (tc && c->n > 10) return SEM_ERR_ARG;
+    ProbDesc d[8];
+    for (int p = 0; p < np; ++p) fill_desc(c, c->ws[p], b[p], x[p], h1, h2, mixed, tc, d[p]);
+    return enqueue(c, o, d, np, s);
+}
+
+// Device address of the solver state of problem p of the last launch (iters, status).
+const void *sem_solve_state_ptr(const sem_ctx *c, int p, int *iters_off, int *status_off)
+{
+    SolveStateHost *S = (SolveStateHost *)c->solve_dev;
+    *iters_off = (int)offsetof(PState, iters);
+    *status_off = (int)offsetof(PState, status);
+    return &S->st[p];
+}
+
+const void *sem_solve_sync_ptr(const sem_ctx *c)
+{
+    return &((SolveStateHost *)c->solve_dev)->sync;
 }
 
 extern "C" int sem_pcg_solve(sem_ctx *c, const double *b, double *x, double h1, double h2,

@@ -1,21 +1,955 @@
-// tgv.cu -- Taylor-Green vortex stepper (BDF3/EXT3 P_N-P_N, 3/2 dealiasing).
-#include "common.cuh"
+// tgv.cu -- Taylor-Green vortex stepper: BDF3/EXT3 P_N-P_N with 3/2 dealiasing.
+//
+// One step (Sec. 3: "P_N-P_N", "fixed third-order time integration",
+// "dealiasing enabled"; hotspots of Sec. 1.1 Fig. 3), order q = min(step+1, 3):
+//   1. C^n_c   = weak dealiased (u^n . grad) u^n_c on M^3 Gauss points,
+//                M = ceil(3(N+1)/2)                              (k_convect)
+//   2. F_c     = -sum_j a_j C^{n+1-j}_c                          (k_tgv_F)
+//   3. g_c     = dssum(F_c) / dssum(B) + sum_j b_j u^{n+1-j}_c / dt
+//                                                                (k_tgv_g, unique nodes)
+//   4. A p     = dssum( sum_a D_a^T ( B sum_c (dr_a/dx_c) g_c ) )  (k_tgv_divg + PCG)
+//   5. (nu A + b0/dt B) u_c = dssum( F_c + B (sum_j b_j u_c/dt - dp/dx_c) )
+//                                                   (k_tgv_vrhs + 3-problem batched PCG)
+//   6. shift histories; KE and enstrophy into a device log      (k_tgv_diag_*)
+// Histories, right-hand sides and diagnostics are FP64.  With op = SEM_F32 the
+// convective term is computed in FP32 and the solves run an FP32 inner PCG
+// inside FP64 refinement.  Steady-state steps (q = 3) are captured once into
+// a CUDA graph and replayed.  Orders N <= 9.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
 
-extern "C" int sem_tgv_init(sem_ctx *, double, double, sem_dtype, const sem_solve_opts *,
-                            const sem_solve_opts *, sem_tgv **out)
+#include "common.cuh"
+#include "gs.cuh"
+
+GsDesc sem_gs_desc(const sem_ctx *c);
+int sem_run_geometry(sem_ctx *c, double *xyz, bool with_jinv, cudaStream_t s);
+int sem_alloc_ws(sem_ctx *c, int slot);
+int sem_dssum_dev(sem_ctx *c, void *u, sem_dtype dt, cudaStream_t s);
+int sem_pcg_solve_dev(sem_ctx *c, int slot, const double *b, double *x, double h1, double h2,
+                      const sem_solve_opts &o, cudaStream_t s);
+int sem_pcg_solve_dev_batch(sem_ctx *c, int np, const double *const *b, double *const *x, double h1,
+                            double h2, const sem_solve_opts &o, cudaStream_t s);
+const void *sem_solve_state_ptr(const sem_ctx *c, int p, int *iters_off, int *status_off);
+const void *sem_solve_sync_ptr(const sem_ctx *c);
+
+#define TGV_LOG 4096
+
+struct TgvLogEntry {
+    double t, ke, en;
+    int iters[4];
+    int status;
+    int pad;
+};
+
+struct TgvDev {       // device-side counters
+    long long count;  // entries written so far
+    double t;
+};
+
+struct sem_tgv {
+    sem_ctx *c;
+    double nu, dt;
+    sem_dtype op;
+    sem_solve_opts vo, po;
+    int step, M;
+    double t;
+    double *u[3][3], *C[3][3], *p, *unew[3], *F[3], *g[3], *bp, *rhs[3];
+    double *part;      // [E][2]
+    double *tab64;     // eta[M], wq[M], J[M*n]
+    float *tab32;
+    TgvLogEntry *log;  // device ring
+    TgvLogEntry *hlog; // pinned host copy
+    TgvDev *dev;
+    cudaGraphExec_t graph;
+    cudaStream_t graph_stream;
+    int graph_state;   // 0 not tried, 1 ready, -1 unavailable
+    double *block;     // one allocation for all fields
+};
+
+// ---------------------------------------------------------------------------
+// 1-D tables of the dealiasing grid (host)
+// ---------------------------------------------------------------------------
+
+// Gauss-Legendre points and weights by Newton on P_M.
+static void gl_table(int M, double *eta, double *wq)
 {
-    if (out) *out = nullptr;
+    for (int q = 0; q < M; ++q) {
+        double x = -cos(M_PI * (q + 0.75) / (M + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 1; k < M; ++k) {
+                double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = M * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-17) break;
+        }
+        double p0 = 1.0, p1 = x;
+        for (int k = 1; k < M; ++k) {
+            double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = M * (x * p1 - p0) / (x * x - 1.0);
+        eta[q] = x;
+        wq[q] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    for (int q = 0; q < M / 2; ++q) {
+        double s = 0.5 * (eta[M - 1 - q] - eta[q]);
+        eta[q] = -s;
+        eta[M - 1 - q] = s;
+        double w = 0.5 * (wq[q] + wq[M - 1 - q]);
+        wq[q] = wq[M - 1 - q] = w;
+    }
+    if (M % 2 == 1) eta[M / 2] = 0.0;
+}
+
+// J[q][j] = l_j(eta_q) on the GLL nodes xi (barycentric form).
+static void interp_table(int n, const double *xi, int M, const double *eta, double *J)
+{
+    double lam[SEM_NPMAX];
+    for (int j = 0; j < n; ++j) {
+        double pr = 1.0;
+        for (int k = 0; k < n; ++k)
+            if (k != j) pr *= (xi[j] - xi[k]);
+        lam[j] = 1.0 / pr;
+    }
+    for (int q = 0; q < M; ++q) {
+        int hit = -1;
+        for (int j = 0; j < n; ++j)
+            if (eta[q] == xi[j]) hit = j;
+        double den = 0.0;
+        for (int j = 0; j < n; ++j)
+            if (hit < 0) den += lam[j] / (eta[q] - xi[j]);
+        for (int j = 0; j < n; ++j)
+            J[q * n + j] = hit >= 0 ? (j == hit ? 1.0 : 0.0) : (lam[j] / (eta[q] - xi[j])) / den;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dealiased convective term
+// ---------------------------------------------------------------------------
+
+template <int NP>
+struct ConvCfg {
+    static constexpr int M = (3 * NP + 1) / 2;
+    static constexpr int N3 = NP * NP * NP, M3 = M * M * M;
+    static constexpr int T1 = NP * NP * M, T2 = NP * M * M;
+    template <typename T>
+    static constexpr size_t smem()
+    {
+        return sizeof(T) * (size_t)(3 * N3 + 3 * N3 + 3 * M3 + M3 + T1 + T2 + M * NP + NP * NP + M + M + 32);
+    }
+};
+
+struct ConvArgs {
+    const double *u[3];
+    double *C[3];
+    const void *jinv;  // [E][9][n3], FP64 or FP32 per T
+    const double *vert;
+    const void *D;     // n*n (T)
+    const void *tab;   // eta[M], wq[M], J[M*n] (T)
+    int nelx, nely;
+    int64_t E;
+};
+
+// v = (J x J x J) in  (n^3 -> M^3); fin(q, value) receives each output.
+template <int NP, typename T, class Fin>
+__device__ __forceinline__ void interp_fwd(const T *in, T *st1, T *st2, const T *sJ, Fin fin)
+{
+    using C = ConvCfg<NP>;
+    constexpr int M = C::M;
+    for (int t = threadIdx.x; t < C::T1; t += blockDim.x) {
+        const int q1 = t % M, j = (t / M) % NP, k = t / (M * NP);
+        T s = 0;
+#pragma unroll
+        for (int l = 0; l < NP; ++l) s = fma(sJ[q1 * NP + l], in[(k * NP + j) * NP + l], s);
+        st1[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < C::T2; t += blockDim.x) {
+        const int q1 = t % M, q2 = (t / M) % M, k = t / (M * M);
+        T s = 0;
+#pragma unroll
+        for (int l = 0; l < NP; ++l) s = fma(sJ[q2 * NP + l], st1[(k * NP + l) * M + q1], s);
+        st2[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < C::M3; t += blockDim.x) {
+        const int q1 = t % M, q2 = (t / M) % M, q3 = t / (M * M);
+        T s = 0;
+#pragma unroll
+        for (int l = 0; l < NP; ++l) s = fma(sJ[q3 * NP + l], st2[(l * M + q2) * M + q1], s);
+        fin(t, s);
+    }
+    __syncthreads();
+}
+
+// out = (J^T x J^T x J^T) f  (M^3 -> n^3).
+template <int NP, typename T, class Fin>
+__device__ __forceinline__ void interp_bwd(const T *f, T *st1, T *st2, const T *sJ, Fin fin)
+{
+    using C = ConvCfg<NP>;
+    constexpr int M = C::M;
+    for (int t = threadIdx.x; t < C::T2; t += blockDim.x) {  // [q3][q2][i]
+        const int i = t % NP, q2 = (t / NP) % M, q3 = t / (NP * M);
+        T s = 0;
+#pragma unroll 4
+        for (int q = 0; q < M; ++q) s = fma(sJ[q * NP + i], f[(q3 * M + q2) * M + q], s);
+        st2[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < C::T1; t += blockDim.x) {  // [q3][j][i]
+        const int i = t % NP, j = (t / NP) % NP, q3 = t / (NP * NP);
+        T s = 0;
+#pragma unroll 4
+        for (int q = 0; q < M; ++q) s = fma(sJ[q * NP + j], st2[(q3 * M + q) * NP + i], s);
+        st1[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < C::N3; t += blockDim.x) {
+        const int i = t % NP, j = (t / NP) % NP, k = t / (NP * NP);
+        T s = 0;
+#pragma unroll 4
+        for (int q = 0; q < M; ++q) s = fma(sJ[q * NP + k], st1[(q * NP + j) * NP + i], s);
+        fin(t, s);
+    }
+    __syncthreads();
+}
+
+template <int NP, typename T>
+__global__ void __launch_bounds__(256) k_convect(ConvArgs a)
+{
+    using C = ConvCfg<NP>;
+    constexpr int M = C::M, N3 = C::N3, M3 = C::M3;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *su = reinterpret_cast<T *>(smem);  // [3][N3]
+    T *sg = su + 3 * N3;                  // [3][N3]
+    T *sfu = sg + 3 * N3;                 // [3][M3] : W|J| u_d on the fine grid
+    T *sf = sfu + 3 * M3;                 // [M3]
+    T *st1 = sf + M3, *st2 = st1 + C::T1;
+    T *sJ = st2 + C::T2, *sD = sJ + M * NP, *seta = sD + NP * NP, *sw = seta + M;
+    T *sc = sw + M;                       // trilinear coefficients [8][3]
+    const T *D = (const T *)a.D, *tab = (const T *)a.tab;
+    for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sD[t] = D[t];
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+        seta[t] = tab[t];
+        sw[t] = tab[M + t];
+    }
+    for (int t = threadIdx.x; t < M * NP; t += blockDim.x) sJ[t] = tab[2 * M + t];
+    const T *jinv = (const T *)a.jinv;
+    for (int64_t e = blockIdx.x; e < a.E; e += gridDim.x) {
+        __syncthreads();
+        const int64_t off = e * N3;
+        for (int t = threadIdx.x; t < 3 * N3; t += blockDim.x) su[t] = (T)a.u[t / N3][off + t % N3];
+        if (threadIdx.x < 24) {  // x = c0 + c1 r + c2 s + c3 t + c4 rs + c5 rt + c6 st + c7 rst
+            const int m = threadIdx.x / 3, d = threadIdx.x % 3;
+            const int ex = (int)(e % a.nelx), ey = (int)((e / a.nelx) % a.nely),
+                      ez = (int)(e / ((int64_t)a.nelx * a.nely));
+            double s = 0.0;
+            for (int cz = 0; cz < 2; ++cz)
+                for (int cy = 0; cy < 2; ++cy)
+                    for (int cx = 0; cx < 2; ++cx) {
+                        const int64_t vi = ((int64_t)(ez + cz) * (a.nely + 1) + (ey + cy)) * (a.nelx + 1) + (ex + cx);
+                        const double sx = cx ? 1.0 : -1.0, sy = cy ? 1.0 : -1.0, sz = cz ? 1.0 : -1.0;
+                        const double sg8[8] = {1.0, sx, sy, sz, sx * sy, sx * sz, sy * sz, sx * sy * sz};
+                        s += sg8[m] * 0.125 * a.vert[vi * 3 + d];
+                    }
+            sc[m * 3 + d] = (T)s;
+        }
+        __syncthreads();
+        // fine-grid velocity, scaled by the quadrature weight and |J|
+        for (int d = 0; d < 3; ++d)
+            interp_fwd<NP, T>(su + d * N3, st1, st2, sJ, [&](int q, T v) { sfu[d * M3 + q] = v; });
+        for (int q = threadIdx.x; q < M3; q += blockDim.x) {
+            const int q1 = q % M, q2 = (q / M) % M, q3 = q / (M * M);
+            const T r = seta[q1], s = seta[q2], t = seta[q3];
+            T J[3][3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                J[d][0] = sc[1 * 3 + d] + sc[4 * 3 + d] * s + sc[5 * 3 + d] * t + sc[7 * 3 + d] * s * t;
+                J[d][1] = sc[2 * 3 + d] + sc[4 * 3 + d] * r + sc[6 * 3 + d] * t + sc[7 * 3 + d] * r * t;
+                J[d][2] = sc[3 * 3 + d] + sc[5 * 3 + d] * r + sc[6 * 3 + d] * s + sc[7 * 3 + d] * r * s;
+            }
+            const T det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                          J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                          J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+            const T wd = sw[q1] * sw[q2] * sw[q3] * det;
+            sfu[q] *= wd;
+            sfu[M3 + q] *= wd;
+            sfu[2 * M3 + q] *= wd;
+        }
+        __syncthreads();
+        for (int c = 0; c < 3; ++c) {
+            // physical gradient of u_c on the GLL nodes
+            const T *uc = su + c * N3;
+            for (int pn = threadIdx.x; pn < N3; pn += blockDim.x) {
+                const int i = pn % NP, j = (pn / NP) % NP, k = pn / (NP * NP);
+                T gr = 0, gs = 0, gt = 0;
+#pragma unroll
+                for (int l = 0; l < NP; ++l) {
+                    gr = fma(sD[i * NP + l], uc[(k * NP + j) * NP + l], gr);
+                    gs = fma(sD[j * NP + l], uc[(k * NP + l) * NP + i], gs);
+                    gt = fma(sD[k * NP + l], uc[(l * NP + j) * NP + i], gt);
+                }
+                const T *ji = jinv + e * 9 * N3 + pn;
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    sg[d * N3 + pn] = ji[(0 * 3 + d) * N3] * gr + ji[(1 * 3 + d) * N3] * gs +
+                                      ji[(2 * 3 + d) * N3] * gt;
+            }
+            for (int q = threadIdx.x; q < M3; q += blockDim.x) sf[q] = 0;
+            __syncthreads();
+            for (int d = 0; d < 3; ++d)
+                interp_fwd<NP, T>(sg + d * N3, st1, st2, sJ,
+                                  [&](int q, T v) { sf[q] = fma(sfu[d * M3 + q], v, sf[q]); });
+            double *Cc = a.C[c] + off;
+            interp_bwd<NP, T>(sf, st1, st2, sJ, [&](int pn, T v) { Cc[pn] = (double)v; });
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise / element kernels of the step
+// ---------------------------------------------------------------------------
+
+struct Coef {
+    double a[3], b[3], b0, dt;
+};
+
+__global__ void k_tgv_F(const double *C00, const double *C01, const double *C02, const double *C10,
+                        const double *C11, const double *C12, const double *C20, const double *C21,
+                        const double *C22, double *F0, double *F1, double *F2, Coef k, int64_t nL)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nL) return;
+    F0[q] = -(k.a[0] * C00[q] + k.a[1] * C10[q] + k.a[2] * C20[q]);
+    F1[q] = -(k.a[0] * C01[q] + k.a[1] * C11[q] + k.a[2] * C21[q]);
+    F2[q] = -(k.a[0] * C02[q] + k.a[1] * C12[q] + k.a[2] * C22[q]);
+}
+
+struct GArgs {
+    const double *F[3];
+    const double *u[3][3];  // [level][comp]
+    double *g[3];
+    const double *geo64;
+    GsDesc gs;
+    Coef k;
+};
+
+// g_c = dssum(F_c) / dssum(B) + sum_j b_j u^{n+1-j}_c / dt at every copy.
+__global__ void k_tgv_g(GArgs a)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= a.gs.nG) return;
+    int64_t idx[8];
+    const int m = gs_copies(a.gs, g, idx);
+    const int n3 = a.gs.n * a.gs.n * a.gs.n;
+    double bs = 0.0;
+    for (int t = 0; t < m; ++t) {
+        const int64_t e = idx[t] / n3;
+        bs += a.geo64[(e * 7 + 6) * n3 + (idx[t] - e * n3)];
+    }
+    const int64_t f = idx[0];
+    for (int c = 0; c < 3; ++c) {
+        double s = 0.0;
+        for (int t = 0; t < m; ++t) s += a.F[c][idx[t]];
+        const double hist = a.k.b[0] * a.u[0][c][f] + a.k.b[1] * a.u[1][c][f] + a.k.b[2] * a.u[2][c][f];
+        const double v = s / bs + hist / a.k.dt;
+        for (int t = 0; t < m; ++t) a.g[c][idx[t]] = v;
+    }
+}
+
+// bp = sum_a D_a^T ( B sum_c (dr_a/dx_c) g_c )   (local, one block per element)
+template <int NP>
+__global__ void k_tgv_divg(const double *g0, const double *g1, const double *g2,
+                           const double *jinv, const double *geo64, const double *D, double *bp,
+                           int64_t E)
+{
+    constexpr int N3 = NP * NP * NP;
+    __shared__ double sh[3 * N3];
+    __shared__ double sD[NP * NP];
+    for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sD[t] = D[t];
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        __syncthreads();
+        const int64_t off = e * N3;
+        for (int pn = threadIdx.x; pn < N3; pn += blockDim.x) {
+            const double gv[3] = {g0[off + pn], g1[off + pn], g2[off + pn]};
+            const double bm = geo64[(e * 7 + 6) * N3 + pn];
+            const double *ji = jinv + e * 9 * N3 + pn;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                sh[a * N3 + pn] = bm * (ji[(a * 3 + 0) * N3] * gv[0] + ji[(a * 3 + 1) * N3] * gv[1] +
+                                        ji[(a * 3 + 2) * N3] * gv[2]);
+        }
+        __syncthreads();
+        for (int pn = threadIdx.x; pn < N3; pn += blockDim.x) {
+            const int i = pn % NP, j = (pn / NP) % NP, k = pn / (NP * NP);
+            double s = 0.0;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) {
+                s += sD[l * NP + i] * sh[0 * N3 + (k * NP + j) * NP + l];
+                s += sD[l * NP + j] * sh[1 * N3 + (k * NP + l) * NP + i];
+                s += sD[l * NP + k] * sh[2 * N3 + (l * NP + j) * NP + i];
+            }
+            bp[off + pn] = s;
+        }
+    }
+}
+
+struct VArgs {
+    const double *F[3];
+    const double *u[3][3];
+    const double *p;
+    const double *jinv, *geo64, *D;
+    double *rhs[3];
+    Coef k;
+    int64_t E;
+};
+
+// rhs_c = F_c + B ( sum_j b_j u_c / dt - dp/dx_c )   (local, one block per element)
+template <int NP>
+__global__ void k_tgv_vrhs(VArgs a)
+{
+    constexpr int N3 = NP * NP * NP;
+    __shared__ double sp[N3];
+    __shared__ double sD[NP * NP];
+    for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sD[t] = a.D[t];
+    for (int64_t e = blockIdx.x; e < a.E; e += gridDim.x) {
+        __syncthreads();
+        const int64_t off = e * N3;
+        for (int pn = threadIdx.x; pn < N3; pn += blockDim.x) sp[pn] = a.p[off + pn];
+        __syncthreads();
+        for (int pn = threadIdx.x; pn < N3; pn += blockDim.x) {
+            const int i = pn % NP, j = (pn / NP) % NP, k = pn / (NP * NP);
+            double gr = 0, gs = 0, gt = 0;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) {
+                gr += sD[i * NP + l] * sp[(k * NP + j) * NP + l];
+                gs += sD[j * NP + l] * sp[(k * NP + l) * NP + i];
+                gt += sD[k * NP + l] * sp[(l * NP + j) * NP + i];
+            }
+            const double *ji = a.jinv + e * 9 * N3 + pn;
+            const double bm = a.geo64[(e * 7 + 6) * N3 + pn];
+            const int64_t q = off + pn;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double dpdx = ji[(0 * 3 + c) * N3] * gr + ji[(1 * 3 + c) * N3] * gs +
+                                    ji[(2 * 3 + c) * N3] * gt;
+                const double hist = a.k.b[0] * a.u[0][c][q] + a.k.b[1] * a.u[1][c][q] +
+                                    a.k.b[2] * a.u[2][c][q];
+                a.rhs[c][q] = a.F[c][q] + bm * (hist / a.k.dt - dpdx);
+            }
+        }
+    }
+}
+
+// Per-element sum of B|u|^2 and B|curl u|^2.
+template <int NP>
+__global__ void k_tgv_diag_part(const double *u0, const double *u1, const double *u2,
+                                const double *jinv, const double *geo64, const double *D,
+                                double *part, int64_t E)
+{
+    constexpr int N3 = NP * NP * NP;
+    __shared__ double su[3 * N3];
+    __shared__ double sD[NP * NP];
+    __shared__ double sred[2 * 32];
+    for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sD[t] = D[t];
+    const double *uu[3] = {u0, u1, u2};
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        __syncthreads();
+        const int64_t off = e * N3;
+        for (int t = threadIdx.x; t < 3 * N3; t += blockDim.x) su[t] = uu[t / N3][off + t % N3];
+        __syncthreads();
+        double ke = 0.0, en = 0.0;
+        for (int pn = threadIdx.x; pn < N3; pn += blockDim.x) {
+            const int i = pn % NP, j = (pn / NP) % NP, k = pn / (NP * NP);
+            const double *ji = jinv + e * 9 * N3 + pn;
+            double du[3][3];  // du[c][d] = du_c / dx_d
+            for (int c = 0; c < 3; ++c) {
+                const double *uc = su + c * N3;
+                double gr = 0, gs = 0, gt = 0;
+#pragma unroll
+                for (int l = 0; l < NP; ++l) {
+                    gr += sD[i * NP + l] * uc[(k * NP + j) * NP + l];
+                    gs += sD[j * NP + l] * uc[(k * NP + l) * NP + i];
+                    gt += sD[k * NP + l] * uc[(l * NP + j) * NP + i];
+                }
+                for (int d = 0; d < 3; ++d)
+                    du[c][d] = ji[(0 * 3 + d) * N3] * gr + ji[(1 * 3 + d) * N3] * gs + ji[(2 * 3 + d) * N3] * gt;
+            }
+            const double wx = du[2][1] - du[1][2], wy = du[0][2] - du[2][0], wz = du[1][0] - du[0][1];
+            const double bm = geo64[(e * 7 + 6) * N3 + pn];
+            ke += bm * (su[pn] * su[pn] + su[N3 + pn] * su[N3 + pn] + su[2 * N3 + pn] * su[2 * N3 + pn]);
+            en += bm * (wx * wx + wy * wy + wz * wz);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            ke += __shfl_xor_sync(0xffffffffu, ke, o);
+            en += __shfl_xor_sync(0xffffffffu, en, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            sred[2 * (threadIdx.x >> 5)] = ke;
+            sred[2 * (threadIdx.x >> 5) + 1] = en;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0, b = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                a += sred[2 * w];
+                b += sred[2 * w + 1];
+            }
+            part[2 * e] = a;
+            part[2 * e + 1] = b;
+        }
+    }
+}
+
+// Fixed-order sum of the element partials into the log; advances time and count.
+__global__ void k_tgv_diag_final(const double *part, int64_t E, double V, double dt, TgvDev *dv,
+                                 TgvLogEntry *log, int advance)
+{
+    __shared__ double s[2][256];
+    double a = 0.0, b = 0.0;
+    for (int64_t e = threadIdx.x; e < E; e += blockDim.x) {
+        a += part[2 * e];
+        b += part[2 * e + 1];
+    }
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + o];
+            s[1][threadIdx.x] += s[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        TgvLogEntry &L = log[dv->count % TGV_LOG];
+        if (advance) dv->t += dt;
+        L.t = dv->t;
+        L.ke = s[0][0] / (2.0 * V);
+        L.en = s[1][0] / (2.0 * V);
+        if (advance) dv->count += 1;
+    }
+}
+
+// Copies solver iteration counts / status of problems p0..p0+np-1 into the current log entry.
+__global__ void k_tgv_log_iters(const char *state, int stride, int iters_off, int status_off,
+                                const int *sync_err, int slot0, int np, TgvDev *dv,
+                                TgvLogEntry *log, int reset)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    TgvLogEntry &L = log[dv->count % TGV_LOG];
+    if (reset) L.status = 0;
+    for (int p = 0; p < np; ++p) {
+        const char *S = state + (size_t)p * stride;
+        L.iters[slot0 + p] = *(const int *)(S + iters_off);
+        int st = *sync_err ? *sync_err : *(const int *)(S + status_off);
+        if (st != 0 && L.status == 0) L.status = st;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+template <int NP>
+static size_t conv_smem(bool f32)
+{
+    return f32 ? ConvCfg<NP>::template smem<float>() : ConvCfg<NP>::template smem<double>();
+}
+
+template <int NP>
+static int launch_convect(sem_tgv *T, const double *const u[3], double *const C[3], cudaStream_t s)
+{
+    sem_ctx *c = T->c;
+    const bool f32 = T->op != SEM_F64;
+    const size_t smem = conv_smem<NP>(f32);
+    if (smem > 227 * 1024) return SEM_ERR_ARG;
+    ConvArgs a;
+    for (int k = 0; k < 3; ++k) {
+        a.u[k] = u[k];
+        a.C[k] = C[k];
+    }
+    a.vert = c->vert;
+    a.nelx = c->nelx;
+    a.nely = c->nely;
+    a.E = c->E;
+    const int grid = (int)(c->E < (int64_t)c->num_sms * 8 ? c->E : (int64_t)c->num_sms * 8);
+    if (f32) {
+        a.jinv = c->jinv32;
+        a.D = c->tab32 + 2 * c->n;
+        a.tab = T->tab32;
+        static bool attr = false;
+        if (!attr) {
+            SEM_CUDA(cudaFuncSetAttribute(k_convect<NP, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = true;
+        }
+        k_convect<NP, float><<<grid, 256, smem, s>>>(a);
+    } else {
+        a.jinv = c->jinv64;
+        a.D = c->tab64 + 2 * c->n;
+        a.tab = T->tab64;
+        static bool attr = false;
+        if (!attr) {
+            SEM_CUDA(cudaFuncSetAttribute(k_convect<NP, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = true;
+        }
+        k_convect<NP, double><<<grid, 256, smem, s>>>(a);
+    }
+    SEM_CHECK_LAUNCH();
+    return SEM_OK;
+}
+
+#define TGV_DISPATCH(npval, ...)            \
+    switch (npval) {                        \
+        SEM_NP_CASE(2, __VA_ARGS__)         \
+        SEM_NP_CASE(3, __VA_ARGS__)         \
+        SEM_NP_CASE(4, __VA_ARGS__)         \
+        SEM_NP_CASE(5, __VA_ARGS__)         \
+        SEM_NP_CASE(6, __VA_ARGS__)         \
+        SEM_NP_CASE(7, __VA_ARGS__)         \
+        SEM_NP_CASE(8, __VA_ARGS__)         \
+        SEM_NP_CASE(9, __VA_ARGS__)         \
+        SEM_NP_CASE(10, __VA_ARGS__)        \
+        default: return SEM_ERR_ARG;        \
+    }
+
+static int convect(sem_tgv *T, const double *const u[3], double *const C[3], cudaStream_t s)
+{
+    TGV_DISPATCH(T->c->n, return launch_convect<NP>(T, u, C, s));
     return SEM_ERR_ARG;
 }
-extern "C" int sem_tgv_set(sem_tgv *, int, const double *, const double *, const double *,
-                           const double *, int, double, void *)
+
+static Coef coef(int q, double dt)
 {
-    return SEM_ERR_ARG;
+    Coef k;
+    memset(&k, 0, sizeof(k));
+    k.dt = dt;
+    if (q == 1) { k.b0 = 1.0; k.b[0] = 1.0; k.a[0] = 1.0; }
+    else if (q == 2) { k.b0 = 1.5; k.b[0] = 2.0; k.b[1] = -0.5; k.a[0] = 2.0; k.a[1] = -1.0; }
+    else { k.b0 = 11.0 / 6.0; k.b[0] = 3.0; k.b[1] = -1.5; k.b[2] = 1.0 / 3.0; k.a[0] = 3.0; k.a[1] = -3.0; k.a[2] = 1.0; }
+    return k;
 }
-extern "C" int sem_tgv_step(sem_tgv *, int, sem_tgv_diag *, void *) { return SEM_ERR_ARG; }
-extern "C" int sem_tgv_get(sem_tgv *, double *, double *, double *, double *, void *)
+
+static int diag(sem_tgv *T, int advance, cudaStream_t s)
 {
-    return SEM_ERR_ARG;
+    sem_ctx *c = T->c;
+    const int blocks = (int)(c->E < 65535 * 16 ? c->E : 65535 * 16);
+    TGV_DISPATCH(c->n, k_tgv_diag_part<NP><<<blocks, 256, 0, s>>>(T->u[0][0], T->u[0][1], T->u[0][2],
+                                                                c->jinv64, c->geo64, c->tab64 + 2 * c->n,
+                                                                T->part, c->E));
+    SEM_CHECK_LAUNCH();
+    const double V = c->volume;
+    k_tgv_diag_final<<<1, 256, 0, s>>>(T->part, c->E, V, T->dt, T->dev, T->log, advance);
+    SEM_CHECK_LAUNCH();
+    return SEM_OK;
 }
-extern "C" int sem_tgv_energy(sem_tgv *, double *, double *, void *) { return SEM_ERR_ARG; }
-extern "C" void sem_tgv_destroy(sem_tgv *) {}
+
+// One step of order q on stream s (capturable).
+static int step_once(sem_tgv *T, int q, cudaStream_t s)
+{
+    sem_ctx *c = T->c;
+    const int64_t nL = c->nL;
+    const size_t bytes = sizeof(double) * nL;
+    const Coef k = coef(q, T->dt);
+    int rc;
+    // 1. convective term of the current velocity
+    rc = convect(T, T->u[0], T->C[0], s);
+    if (rc) return rc;
+    // 2. extrapolated convection
+    k_tgv_F<<<(unsigned)sem_ceil_div(nL, 256), 256, 0, s>>>(
+        T->C[0][0], T->C[0][1], T->C[0][2], T->C[1][0], T->C[1][1], T->C[1][2], T->C[2][0],
+        T->C[2][1], T->C[2][2], T->F[0], T->F[1], T->F[2], k, nL);
+    SEM_CHECK_LAUNCH();
+    // 3. strong right-hand side g
+    GArgs ga;
+    for (int cc = 0; cc < 3; ++cc) {
+        ga.F[cc] = T->F[cc];
+        ga.g[cc] = T->g[cc];
+        for (int l = 0; l < 3; ++l) ga.u[l][cc] = T->u[l][cc];
+    }
+    ga.geo64 = c->geo64;
+    ga.gs = sem_gs_desc(c);
+    ga.k = k;
+    k_tgv_g<<<(unsigned)sem_ceil_div(c->nG, 256), 256, 0, s>>>(ga);
+    SEM_CHECK_LAUNCH();
+    // 4. pressure: weak divergence, dssum, Poisson solve from p^n
+    const int blocks = (int)(c->E < 65535 * 16 ? c->E : 65535 * 16);
+    TGV_DISPATCH(c->n, k_tgv_divg<NP><<<blocks, 256, 0, s>>>(T->g[0], T->g[1], T->g[2], c->jinv64,
+                                                             c->geo64, c->tab64 + 2 * c->n, T->bp, c->E));
+    SEM_CHECK_LAUNCH();
+    rc = sem_dssum_dev(c, T->bp, SEM_F64, s);
+    if (rc) return rc;
+    rc = sem_pcg_solve_dev(c, 0, T->bp, T->p, 1.0, 0.0, T->po, s);
+    if (rc) return rc;
+    int io, so;
+    const char *st0 = (const char *)sem_solve_state_ptr(c, 0, &io, &so);
+    const char *st1 = (const char *)sem_solve_state_ptr(c, 1, &io, &so);
+    const int stride = (int)(st1 - st0);
+    const int *serr = (const int *)((const char *)sem_solve_sync_ptr(c) + 8);
+    k_tgv_log_iters<<<1, 32, 0, s>>>(st0, stride, io, so, serr, 0, 1, T->dev, T->log, 1);
+    SEM_CHECK_LAUNCH();
+    // 5. velocity right-hand sides and the three Helmholtz solves from u^n
+    VArgs va;
+    for (int cc = 0; cc < 3; ++cc) {
+        va.F[cc] = T->F[cc];
+        va.rhs[cc] = T->rhs[cc];
+        for (int l = 0; l < 3; ++l) va.u[l][cc] = T->u[l][cc];
+    }
+    va.p = T->p;
+    va.jinv = c->jinv64;
+    va.geo64 = c->geo64;
+    va.D = c->tab64 + 2 * c->n;
+    va.k = k;
+    va.E = c->E;
+    TGV_DISPATCH(c->n, k_tgv_vrhs<NP><<<blocks, 256, 0, s>>>(va));
+    SEM_CHECK_LAUNCH();
+    for (int cc = 0; cc < 3; ++cc) {
+        rc = sem_dssum_dev(c, T->rhs[cc], SEM_F64, s);
+        if (rc) return rc;
+        SEM_CUDA(cudaMemcpyAsync(T->unew[cc], T->u[0][cc], bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    const double *bb[3] = {T->rhs[0], T->rhs[1], T->rhs[2]};
+    double *xx[3] = {T->unew[0], T->unew[1], T->unew[2]};
+    rc = sem_pcg_solve_dev_batch(c, 3, bb, xx, T->nu, k.b0 / T->dt, T->vo, s);
+    if (rc) return rc;
+    k_tgv_log_iters<<<1, 32, 0, s>>>(st0, stride, io, so, serr, 1, 3, T->dev, T->log, 0);
+    SEM_CHECK_LAUNCH();
+    // 6. shift histories (copies keep every buffer address fixed for graph replay)
+    for (int cc = 0; cc < 3; ++cc) {
+        SEM_CUDA(cudaMemcpyAsync(T->u[2][cc], T->u[1][cc], bytes, cudaMemcpyDeviceToDevice, s));
+        SEM_CUDA(cudaMemcpyAsync(T->u[1][cc], T->u[0][cc], bytes, cudaMemcpyDeviceToDevice, s));
+        SEM_CUDA(cudaMemcpyAsync(T->u[0][cc], T->unew[cc], bytes, cudaMemcpyDeviceToDevice, s));
+        SEM_CUDA(cudaMemcpyAsync(T->C[2][cc], T->C[1][cc], bytes, cudaMemcpyDeviceToDevice, s));
+        SEM_CUDA(cudaMemcpyAsync(T->C[1][cc], T->C[0][cc], bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    return diag(T, 1, s);
+}
+
+extern "C" void sem_tgv_destroy(sem_tgv *T)
+{
+    if (!T) return;
+    cudaDeviceSynchronize();
+    if (T->graph_state == 1) cudaGraphExecDestroy(T->graph);
+    if (T->block) cudaFree(T->block);
+    if (T->part) cudaFree(T->part);
+    if (T->tab64) cudaFree(T->tab64);
+    if (T->tab32) cudaFree(T->tab32);
+    if (T->log) cudaFree(T->log);
+    if (T->dev) cudaFree(T->dev);
+    if (T->hlog) cudaFreeHost(T->hlog);
+    free(T);
+}
+
+extern "C" int sem_tgv_init(sem_ctx *c, double nu, double dt, sem_dtype op, const sem_solve_opts *vel,
+                            const sem_solve_opts *pres, sem_tgv **out)
+{
+    if (!out) return SEM_ERR_ARG;
+    *out = nullptr;
+    if (!c || !(nu > 0) || !(dt > 0) || (op != SEM_F64 && op != SEM_F32)) return SEM_ERR_ARG;
+    if (!c->periodic[0] || !c->periodic[1] || !c->periodic[2] || c->n > 10) return SEM_ERR_ARG;
+    sem_tgv *T = (sem_tgv *)calloc(1, sizeof(sem_tgv));
+    if (!T) return SEM_ERR_NOMEM;
+    T->c = c;
+    T->nu = nu;
+    T->dt = dt;
+    T->op = op;
+    sem_solve_opts_default(&T->vo);
+    sem_solve_opts_default(&T->po);
+    if (vel) T->vo = *vel;
+    if (pres) T->po = *pres;
+    if (op == SEM_F32) {
+        T->vo.inner = SEM_F32;
+        T->po.inner = SEM_F32;
+    }
+    const int n = c->n;
+    T->M = (3 * n + 1) / 2;
+    const int64_t nL = c->nL;
+#define TGV_TRY(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            sem_note_cuda_error(e_, #call);                                                  \
+            sem_tgv_destroy(T);                                                              \
+            return e_ == cudaErrorMemoryAllocation ? SEM_ERR_NOMEM : SEM_ERR_CUDA;           \
+        }                                                                                    \
+    } while (0)
+    // fields: u 9, C 9, p 1, unew 3, F 3, g 3, bp 1, rhs 3 = 32 E-vectors
+    TGV_TRY(cudaMalloc(&T->block, sizeof(double) * 32 * nL));
+    TGV_TRY(cudaMemset(T->block, 0, sizeof(double) * 32 * nL));
+    double *b = T->block;
+    for (int l = 0; l < 3; ++l)
+        for (int k = 0; k < 3; ++k) { T->u[l][k] = b; b += nL; }
+    for (int l = 0; l < 3; ++l)
+        for (int k = 0; k < 3; ++k) { T->C[l][k] = b; b += nL; }
+    T->p = b; b += nL;
+    for (int k = 0; k < 3; ++k) { T->unew[k] = b; b += nL; }
+    for (int k = 0; k < 3; ++k) { T->F[k] = b; b += nL; }
+    for (int k = 0; k < 3; ++k) { T->g[k] = b; b += nL; }
+    T->bp = b; b += nL;
+    for (int k = 0; k < 3; ++k) { T->rhs[k] = b; b += nL; }
+    TGV_TRY(cudaMalloc(&T->part, sizeof(double) * 2 * c->E));
+    // dealiasing tables
+    double eta[64], wq[64], J[64 * SEM_NPMAX], h64[2 * 64 + 64 * SEM_NPMAX];
+    float h32[2 * 64 + 64 * SEM_NPMAX];
+    gl_table(T->M, eta, wq);
+    interp_table(n, c->hxi, T->M, eta, J);
+    const int ntab = 2 * T->M + T->M * n;
+    for (int q = 0; q < T->M; ++q) { h64[q] = eta[q]; h64[T->M + q] = wq[q]; }
+    for (int t = 0; t < T->M * n; ++t) h64[2 * T->M + t] = J[t];
+    for (int t = 0; t < ntab; ++t) h32[t] = (float)h64[t];
+    TGV_TRY(cudaMalloc(&T->tab64, sizeof(double) * ntab));
+    TGV_TRY(cudaMalloc(&T->tab32, sizeof(float) * ntab));
+    TGV_TRY(cudaMemcpy(T->tab64, h64, sizeof(double) * ntab, cudaMemcpyHostToDevice));
+    TGV_TRY(cudaMemcpy(T->tab32, h32, sizeof(float) * ntab, cudaMemcpyHostToDevice));
+    TGV_TRY(cudaMalloc(&T->log, sizeof(TgvLogEntry) * TGV_LOG));
+    TGV_TRY(cudaMemset(T->log, 0, sizeof(TgvLogEntry) * TGV_LOG));
+    TGV_TRY(cudaMallocHost(&T->hlog, sizeof(TgvLogEntry) * TGV_LOG));
+    TGV_TRY(cudaMalloc(&T->dev, sizeof(TgvDev)));
+    TGV_TRY(cudaMemset(T->dev, 0, sizeof(TgvDev)));
+    // J^{-1} on the context and three solver workspaces for the velocity batch
+    if (!c->jinv64) {
+        TGV_TRY(cudaMalloc(&c->jinv64, sizeof(double) * 9 * nL));
+        TGV_TRY(cudaMalloc(&c->jinv32, sizeof(float) * 9 * nL));
+        int rc = sem_run_geometry(c, nullptr, true, 0);
+        if (rc) { sem_tgv_destroy(T); return rc; }
+    }
+    while (c->nws < 3) {
+        int rc = sem_alloc_ws(c, c->nws);
+        if (rc) { sem_tgv_destroy(T); return rc; }
+        c->nws += 1;
+    }
+    TGV_TRY(cudaDeviceSynchronize());
+#undef TGV_TRY
+    *out = T;
+    return SEM_OK;
+}
+
+static int stage_field(sem_ctx *c, const double *src, double *dst, cudaStream_t s)
+{
+    const size_t bytes = sizeof(double) * c->nL;
+    const cudaMemcpyKind kind = sem_is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    SEM_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, s));
+    return SEM_OK;
+}
+
+__global__ void k_tgv_set_time(TgvDev *dv, double t) { dv->t = t; }
+
+extern "C" int sem_tgv_set(sem_tgv *T, int level, const double *u, const double *v, const double *w,
+                           const double *p, int step, double t, void *stream)
+{
+    if (!T || level < 0 || level > 2 || !u || !v || !w || step < 0) return SEM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double *src[3] = {u, v, w};
+    for (int k = 0; k < 3; ++k) {
+        int rc = stage_field(T->c, src[k], T->u[level][k], s);
+        if (rc) return rc;
+    }
+    if (level == 0 && p) {
+        int rc = stage_field(T->c, p, T->p, s);
+        if (rc) return rc;
+    }
+    if (level > 0) {  // history of the convective term at that level
+        int rc = convect(T, T->u[level], T->C[level], s);
+        if (rc) return rc;
+    }
+    if (level == 0) {
+        T->step = step;
+        T->t = t;
+        k_tgv_set_time<<<1, 1, 0, s>>>(T->dev, t);
+        SEM_CHECK_LAUNCH();
+    }
+    SEM_CUDA(cudaStreamSynchronize(s));
+    return SEM_OK;
+}
+
+extern "C" int sem_tgv_step(sem_tgv *T, int nsteps, sem_tgv_diag *out, void *stream)
+{
+    if (!T || nsteps < 0) return SEM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    long long first = -1;
+    SEM_CUDA(cudaMemcpyAsync(&T->hlog[0], T->dev, sizeof(TgvDev), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    first = ((TgvDev *)&T->hlog[0])->count;
+    for (int it = 0; it < nsteps; ++it) {
+        const int q = T->step + 1 < 3 ? T->step + 1 : 3;
+        int rc;
+        if (q == 3 && s != 0 && T->graph_state == 0) {
+            // capture one steady-state step; fall back to direct launches if capture fails
+            cudaGraph_t g = nullptr;
+            T->graph_state = -1;
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                rc = step_once(T, 3, s);
+                cudaError_t ce = cudaStreamEndCapture(s, &g);
+                if (rc == SEM_OK && ce == cudaSuccess && g &&
+                    cudaGraphInstantiate(&T->graph, g, 0) == cudaSuccess) {
+                    T->graph_state = 1;
+                    T->graph_stream = s;
+                }
+                if (g) cudaGraphDestroy(g);
+            }
+            cudaGetLastError();
+        }
+        if (q == 3 && T->graph_state == 1) {
+            SEM_CUDA(cudaGraphLaunch(T->graph, s));
+        } else {
+            rc = step_once(T, q, s);
+            if (rc) return rc;
+        }
+        T->step += 1;
+        T->t += T->dt;
+    }
+    if (!out) return SEM_OK;
+    SEM_CUDA(cudaMemcpyAsync(T->hlog, T->log, sizeof(TgvLogEntry) * TGV_LOG, cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    int worst = SEM_OK;
+    for (int it = 0; it < nsteps; ++it) {
+        const TgvLogEntry &L = T->hlog[(first + it) % TGV_LOG];
+        out[it].t = L.t;
+        out[it].ke = L.ke;
+        out[it].enstrophy = L.en;
+        for (int k = 0; k < 4; ++k) out[it].iters[k] = L.iters[k];
+        out[it].status = L.status;
+        if (L.status != 0 && worst == SEM_OK) worst = L.status;
+    }
+    return worst;
+}
+
+extern "C" int sem_tgv_get(sem_tgv *T, double *u, double *v, double *w, double *p, void *stream)
+{
+    if (!T) return SEM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * T->c->nL;
+    double *dst[4] = {u, v, w, p};
+    const double *src[4] = {T->u[0][0], T->u[0][1], T->u[0][2], T->p};
+    for (int k = 0; k < 4; ++k) {
+        if (!dst[k]) continue;
+        const cudaMemcpyKind kind = sem_is_device_ptr(dst[k]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        SEM_CUDA(cudaMemcpyAsync(dst[k], src[k], bytes, kind, s));
+    }
+    SEM_CUDA(cudaStreamSynchronize(s));
+    return SEM_OK;
+}
+
+extern "C" int sem_tgv_energy(sem_tgv *T, double *ke, double *en, void *stream)
+{
+    if (!T || !ke || !en) return SEM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = diag(T, 0, s);
+    if (rc) return rc;
+    TgvDev h;
+    SEM_CUDA(cudaMemcpyAsync(&h, T->dev, sizeof(TgvDev), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    TgvLogEntry L;
+    SEM_CUDA(cudaMemcpy(&L, T->log + (h.count % TGV_LOG), sizeof(L), cudaMemcpyDeviceToHost));
+    *ke = L.ke;
+    *en = L.en;
+    return SEM_OK;
+}

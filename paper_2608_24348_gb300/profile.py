@@ -1,0 +1,67 @@
+"""Run one hot kernel on a chosen mesh, for profiler captures (ncu) of a small case.
+
+    python -m paper_2608_24348_gb300.profile --kernel ax_f64 --nel 24 --reps 3
+
+Kernels: ax_f64, ax_f32, ax_bf16_tc, dssum, pcg_f64, pcg_f32 (a bounded number
+of PCG iterations), tgv_f64, tgv_f32 (steps of the Taylor-Green stepper).
+The mesh is the benchmark's: nel^3 elements, order N, interior vertices
+perturbed by up to 10%.
+"""
+from __future__ import annotations
+
+import argparse
+import math
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel", default="ax_f64")
+    ap.add_argument("--nel", type=int, default=24)
+    ap.add_argument("--N", type=int, default=7)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--maxit", type=int, default=20)
+    args = ap.parse_args(argv)
+
+    import torch
+
+    from . import inputs, sem
+    dev = torch.device("cuda:0")
+    nel = (args.nel,) * 3
+    tgv = args.kernel.startswith("tgv")
+    v = inputs.box_vertices(nel, (2 * math.pi,) * 3, perturb=0.0 if tgv else 0.1)
+    ctx = sem.Ctx(args.N, nel, (2 * math.pi,) * 3, (1, 1, 1), vertices=v)
+    u = torch.from_numpy(inputs.unique_uniform_field(args.N, nel)).to(dev)
+    if args.kernel.startswith("ax") or args.kernel == "dssum":
+        dt = args.kernel[3:] if args.kernel.startswith("ax") else "f64"
+        x = u if dt == "f64" else u.float()
+        w = torch.empty_like(x)
+        for _ in range(args.reps):
+            if args.kernel == "dssum":
+                ctx.dssum(x, "f64")
+            else:
+                ctx.ax(x, w, 0.01, 1000.0, dt)
+    elif args.kernel.startswith("pcg"):
+        b = torch.empty_like(u)
+        ctx.ax(u, b, 0.0, 1.0, "f64")
+        ctx.dssum(b, "f64")
+        for _ in range(args.reps):
+            x = torch.zeros_like(b)
+            ctx.pcg_solve(b, x, 1.0, 0.0, tol=1e-14, maxit=args.maxit,
+                          inner=args.kernel[4:], inner_tol=1e-4)
+    elif tgv:
+        x, y, z = torch.empty(3 * ctx.nL, dtype=torch.float64, device=dev).view(3, -1)
+        xyz = torch.empty(3 * ctx.nL, dtype=torch.float64, device=dev)
+        ctx.coords(xyz)
+        x, y, z = xyz.view(3, -1)
+        uu, vv, ww, pp = inputs.tgv_initial(x, y, z, lib=torch)
+        T = sem.TGV(ctx, 1.0 / 1600, 1e-3, op=args.kernel[4:])
+        T.set(uu.contiguous(), vv.contiguous(), (ww + 0 * x).contiguous(), pp.contiguous())
+        T.step(args.reps)
+    else:
+        raise SystemExit(f"unknown kernel {args.kernel}")
+    torch.cuda.synchronize()
+    print("done", args.kernel, ctx.nL)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,134 @@
+"""GPU parity of the Taylor-Green vortex stepper (BDF3/EXT3 P_N-P_N, 3/2 dealiasing).
+
+Bars: KE and enstrophy histories against the FP64 oracle by the paper's
+e_E,max / e_Omega,max (Sec. 4.2, without the x100%): <= 1e-4 and <= 1e-3; with
+tight solver tolerances the fields themselves agree to 1e-8.  The exact 2-D
+Taylor-Green solution is reproduced with third-order temporal convergence.
+At full size (32^3, N=7) the t=0 integrals are KE = 1/8 and Omega = 3/8, and
+the mixed-precision run stays within the same e_E,max / e_Omega,max of the
+FP64 run.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import gpu_coords, pair, torch_dev
+from paper_2608_24348_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TWO_PI = 2 * math.pi
+
+
+def e_max(a, ref):
+    a, ref = np.asarray(a), np.asarray(ref)
+    return float(np.abs(a - ref).max() / np.abs(ref).max())
+
+
+def _gpu_tgv(sem, ctx, nu, dt, op="f64", tight=False):
+    if tight:
+        vo = sem.opts(tol=1e-12, abs_tol=False)
+        po = sem.opts(tol=1e-12, abs_tol=False)
+    else:
+        vo = sem.opts(tol=1e-6, abs_tol=True)
+        po = sem.opts(tol=1e-4, abs_tol=True)
+    return sem.TGV(ctx, nu, dt, op=op, vel=vo, pres=po)
+
+
+def _ic_gpu(ctx):
+    torch, _ = torch_dev()
+    x, y, z = gpu_coords(ctx)
+    u, v, w, p = inputs.tgv_initial(x, y, z, lib=torch)
+    return [t.contiguous() for t in (u, v, w + 0 * x, p)]
+
+
+@pytest.mark.parametrize("tight", [False, True])
+def test_tgv_matches_oracle_over_20_steps(sem, tight):
+    torch, dev = torch_dev()
+    N, nel, nu, dt = 7, (6, 6, 6), 1.0 / 1600, 1e-3
+    ctx, m, v = pair(sem, N, nel, 0.0)
+    T = _gpu_tgv(sem, ctx, nu, dt, tight=tight)
+    u, vv, w, p = _ic_gpu(ctx)
+    T.set(u, vv, w, p)
+    torch.cuda.synchronize()
+    d = T.step(20)
+    assert all(r["status"] == 0 for r in d), d
+    x, y, z = m.xyz
+    uo, vo, wo, po = inputs.tgv_initial(x, y, z)
+    tol = dict(tol_v=1e-12, tol_p=1e-12, abs_tol=False) if tight else \
+        dict(tol_v=1e-6, tol_p=1e-4, abs_tol=True)
+    O = oracle.TGV(N, nel, v, (TWO_PI,) * 3, nu, dt, **tol)
+    O.set(uo, vo, wo, po)
+    do = O.step(20)
+    assert np.all(do[:, 7] == 0)
+    ke, en = [r["ke"] for r in d], [r["enstrophy"] for r in d]
+    np.testing.assert_allclose([r["t"] for r in d], do[:, 0], rtol=1e-12)
+    assert e_max(ke, do[:, 1]) <= 1e-4
+    assert e_max(en, do[:, 2]) <= 1e-3
+    if tight:
+        assert e_max(ke, do[:, 1]) <= 1e-10
+        assert e_max(en, do[:, 2]) <= 1e-9
+        out = [torch.empty_like(u) for _ in range(4)]
+        T.get(*out)
+        ref = O.get()
+        for c in range(3):
+            assert e_max(out[c].cpu().numpy(), ref[c]) <= 1e-8
+    else:
+        # pressure iterations within a few of the oracle's (absolute tolerances)
+        assert abs(np.mean([r["iters"][0] for r in d]) - do[:, 3].mean()) <= 3
+
+
+def _tg_gpu_error(sem, nu, dt, T_end, N=9, nel=(4, 4, 1)):
+    torch, dev = torch_dev()
+    ctx, _, _ = pair(sem, N, nel, 0.0, with_oracle=False)
+    T = _gpu_tgv(sem, ctx, nu, dt, tight=True)
+    x, y, z = gpu_coords(ctx)
+    for lev in (2, 1, 0):
+        u, v, w, p = inputs.tg2d_exact(x, y, z, -lev * dt, nu, lib=torch)
+        w = (w + 0 * x).contiguous()
+        T.set(u.contiguous(), v.contiguous(), w, p.contiguous() if lev == 0 else None, level=lev,
+              step=2, t=0.0)
+    nst = int(round(T_end / dt))
+    d = T.step(nst)
+    assert all(r["status"] == 0 for r in d)
+    out = [torch.empty(ctx.nL, dtype=torch.float64, device=dev) for _ in range(4)]
+    T.get(*out)
+    ue, ve, _, _ = inputs.tg2d_exact(x, y, z, T_end, nu, lib=torch)
+    return max(float((out[0] - ue).abs().max()), float((out[1] - ve).abs().max()))
+
+
+def test_tgv_third_order_on_exact_2d_taylor_green(sem):
+    e = [_tg_gpu_error(sem, 0.2, dt, 1.0) for dt in (0.1, 0.05, 0.025)]
+    rates = [math.log2(e[0] / e[1]), math.log2(e[1] / e[2])]
+    assert rates[0] > 2.6 and rates[1] > 2.6, (e, rates)
+
+
+def test_tgv_full_size_initial_integrals_and_mixed_precision(sem):
+    """32^3 elements, N=7: KE(0) = 1/8, Omega(0) = 3/8; 20 steps at Re=1600,
+    dt=1e-3 in FP64 and in mixed precision (FP32 convection and inner solves,
+    FP64 refinement, histories and diagnostics); energy balance."""
+    torch, dev = torch_dev()
+    ctx, _, _ = pair(sem, 7, (32, 32, 32), 0.0, with_oracle=False)
+    nu, dt = 1.0 / 1600, 1e-3
+    runs = {}
+    for op in ("f64", "f32"):
+        T = _gpu_tgv(sem, ctx, nu, dt, op=op)
+        u, v, w, p = _ic_gpu(ctx)
+        T.set(u, v, w, p)
+        ke0, en0 = T.energy()
+        assert abs(ke0 - 0.125) <= 1e-9 and abs(en0 - 0.375) <= 1e-7, (ke0, en0)
+        d = T.step(20)
+        assert all(r["status"] == 0 for r in d), d[-1]
+        runs[op] = (ke0, en0, d)
+        T.close()
+        del u, v, w, p
+    ke0, en0, d = runs["f64"]
+    slope = (d[-1]["ke"] - ke0) / d[-1]["t"]
+    assert abs(slope + 2 * nu * en0) <= 0.02 * 2 * nu * en0
+    k64 = [r["ke"] for r in d]
+    o64 = [r["enstrophy"] for r in d]
+    k32 = [r["ke"] for r in runs["f32"][2]]
+    o32 = [r["enstrophy"] for r in runs["f32"][2]]
+    assert e_max(k32, k64) <= 1e-4
+    assert e_max(o32, o64) <= 1e-3
