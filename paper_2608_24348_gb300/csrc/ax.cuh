@@ -61,7 +61,7 @@ __device__ __forceinline__ void ax_element(const Load &load, const Store &store,
             su[k * NP2 + tid] = ru[k];
         }
     }
-    __syncthreads();
+    __syncthreads();  // publishes the slab and the D tables written before the call
     if (active) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
@@ -96,5 +96,62 @@ __device__ __forceinline__ void ax_element(const Load &load, const Store &store,
             store(k * NP2 + tid, s, ru[k]);
         }
     }
+    __syncthreads();
+}
+
+// Low-register variant: one thread per node (strided over the element),
+// every contraction read from shared memory.  Used where register pressure
+// matters more than speed (the FP64 residual of mixed-precision refinement,
+// evaluated once per refinement step).  smem: u, vr, vs, vt slabs.
+template <int NP>
+__host__ __device__ constexpr size_t ax_lowreg_smem_bytes()
+{
+    return sizeof(double) * (2 * NP * NP + 4 * (size_t)NP * NP * NP);
+}
+
+template <int NP, class Load, class Store>
+__device__ __forceinline__ void ax_element_lowreg(const Load &load, const Store &store,
+                                                  const double *__restrict__ geo, double h1,
+                                                  double h2, const double *__restrict__ D,
+                                                  unsigned char *smem, bool active)
+{
+    constexpr int NP2 = NP * NP, NP3 = NP2 * NP;
+    double *sD = reinterpret_cast<double *>(smem), *sDT = sD + NP2;
+    double *su = sDT + NP2, *svr = su + NP3, *svs = svr + NP3, *svt = svs + NP3;
+    for (int t = threadIdx.x; t < NP2; t += blockDim.x) {
+        const int a = t / NP, b = t - a * NP;
+        sD[t] = D[t];
+        sDT[b * NP + a] = D[t];
+    }
+    if (active)
+        for (int q = threadIdx.x; q < NP3; q += blockDim.x) su[q] = load(q);
+    __syncthreads();
+    if (active)
+        for (int q = threadIdx.x; q < NP3; q += blockDim.x) {
+            const int i = q % NP, j = (q / NP) % NP, k = q / NP2;
+            double ur = 0, us = 0, ut = 0;
+            for (int l = 0; l < NP; ++l) {
+                ur = fma(sDT[l * NP + i], su[(k * NP + j) * NP + l], ur);
+                us = fma(sDT[l * NP + j], su[(k * NP + l) * NP + i], us);
+                ut = fma(sDT[l * NP + k], su[(l * NP + j) * NP + i], ut);
+            }
+            const double g11 = geo[0 * NP3 + q], g22 = geo[1 * NP3 + q], g33 = geo[2 * NP3 + q];
+            const double g12 = geo[3 * NP3 + q], g13 = geo[4 * NP3 + q], g23 = geo[5 * NP3 + q];
+            svr[q] = h1 * (g11 * ur + g12 * us + g13 * ut);
+            svs[q] = h1 * (g12 * ur + g22 * us + g23 * ut);
+            svt[q] = h1 * (g13 * ur + g23 * us + g33 * ut);
+        }
+    __syncthreads();
+    if (active)
+        for (int q = threadIdx.x; q < NP3; q += blockDim.x) {
+            const int i = q % NP, j = (q / NP) % NP, k = q / NP2;
+            double s = h2 * geo[6 * NP3 + q] * su[q];
+            for (int l = 0; l < NP; ++l) {
+                s = fma(sD[l * NP + i], svr[(k * NP + j) * NP + l], s);
+                s = fma(sD[l * NP + j], svs[(k * NP + l) * NP + i], s);
+                s = fma(sD[l * NP + k], svt[(l * NP + j) * NP + i], s);
+            }
+            store(q, s, su[q]);
+        }
     __syncthreads();
 }

@@ -19,13 +19,13 @@
 
 GsDesc sem_gs_desc(const sem_ctx *c);  // ops.cu
 
-#define SEM_DECL_NP(NPV) int sem_solve_launch_np##NPV(const SolveParams<8> &, int, long long, cudaStream_t);
+#define SEM_DECL_NP(NPV) int sem_solve_launch_np##NPV(const SolveParams<8> &, int, int, long long, cudaStream_t);
 SEM_DECL_NP(2) SEM_DECL_NP(3) SEM_DECL_NP(4) SEM_DECL_NP(5) SEM_DECL_NP(6) SEM_DECL_NP(7)
 SEM_DECL_NP(8) SEM_DECL_NP(9) SEM_DECL_NP(10) SEM_DECL_NP(11) SEM_DECL_NP(12) SEM_DECL_NP(13)
 SEM_DECL_NP(14) SEM_DECL_NP(15) SEM_DECL_NP(16)
 #undef SEM_DECL_NP
 
-typedef int (*noalloc_launch_fn)(const SolveParams<8> &, int, long long, cudaStream_t);
+typedef int (*noalloc_launch_fn)(const SolveParams<8> &, int, int, long long, cudaStream_t);
 static const noalloc_launch_fn k_noalloc_launch[17] = {
     nullptr, nullptr, sem_solve_launch_np2, sem_solve_launch_np3, sem_solve_launch_np4,
     sem_solve_launch_np5, sem_solve_launch_np6, sem_solve_launch_np7, sem_solve_launch_np8,
@@ -232,7 +232,7 @@ extern "C" int sem_pcg_solve_noalloc(int N, int nelx, int nely, int nelz, const 
 
     // the array keeps the previous call's contents: the solver state must start at zero
     SEM_CUDA(cudaMemsetAsync(state, 0, sizeof(NaStateHost), s));
-    rc = k_noalloc_launch[n](prm, sms, (nL + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS, s);
+    rc = k_noalloc_launch[n](prm, MODE_F64, sms, (nL + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS, s);
     if (rc) return rc;
     NaStateHost h;
     SEM_CUDA(cudaMemcpyAsync(&h, state, sizeof(NaStateHost), cudaMemcpyDeviceToHost, s));

@@ -10,15 +10,15 @@ GsDesc sem_gs_desc(const sem_ctx *c);  // ops.cu
 int sem_alloc_ws(sem_ctx *c, int slot);  // setup.cu
 
 // Per-order kernels (solve_npXX.cu), up to 8 problems of one order.
-#define SEM_DECL_NP(NPV) int sem_solve_launch_np##NPV(const SolveParams<8> &, int, long long, cudaStream_t);
+#define SEM_DECL_NP(NPV) int sem_solve_launch_np##NPV(const SolveParams<8> &, int, int, long long, cudaStream_t);
 SEM_DECL_NP(2) SEM_DECL_NP(3) SEM_DECL_NP(4) SEM_DECL_NP(5) SEM_DECL_NP(6) SEM_DECL_NP(7)
 SEM_DECL_NP(8) SEM_DECL_NP(9) SEM_DECL_NP(10) SEM_DECL_NP(11) SEM_DECL_NP(12) SEM_DECL_NP(13)
 SEM_DECL_NP(14) SEM_DECL_NP(15) SEM_DECL_NP(16)
 #undef SEM_DECL_NP
 // Mixed-order kernel for N in {5, 7, 9} (solve_multi.cu), up to 64 problems.
-int sem_solve_launch_multi(const SolveParams<SEM_MAXP> &, int, long long, cudaStream_t);
+int sem_solve_launch_multi(const SolveParams<SEM_MAXP> &, int, int, long long, cudaStream_t);
 
-typedef int (*launch8_fn)(const SolveParams<8> &, int, long long, cudaStream_t);
+typedef int (*launch8_fn)(const SolveParams<8> &, int, int, long long, cudaStream_t);
 static const launch8_fn k_launch8[17] = {
     nullptr, nullptr, sem_solve_launch_np2, sem_solve_launch_np3, sem_solve_launch_np4,
     sem_solve_launch_np5, sem_solve_launch_np6, sem_solve_launch_np7, sem_solve_launch_np8,
@@ -133,6 +133,7 @@ static int enqueue(sem_ctx *owner, const sem_solve_opts &o, const ProbDesc *d, i
 {
     SEM_CUDA(cudaMemsetAsync(owner->solve_dev, 0, sizeof(SolveStateHost), s));
     const long long mi = max_items(d, np);
+    const int mode = o.inner == SEM_F64 ? MODE_F64 : (o.inner == SEM_F32 ? MODE_F32 : MODE_TC);
     bool same = true;
     for (int p = 1; p < np; ++p) same &= (d[p].n == d[0].n);
     int rc;
@@ -141,12 +142,12 @@ static int enqueue(sem_ctx *owner, const sem_solve_opts &o, const ProbDesc *d, i
         memset(&prm, 0, sizeof(prm));
         fill_common(prm, owner, o, np);
         for (int p = 0; p < np; ++p) prm.prob[p] = d[p];
-        rc = k_launch8[d[0].n](prm, owner->num_sms, mi, s);
+        rc = k_launch8[d[0].n](prm, mode, owner->num_sms, mi, s);
     } else {
         SolveParams<SEM_MAXP> *prm = new SolveParams<SEM_MAXP>();
         fill_common(*prm, owner, o, np);
         for (int p = 0; p < np; ++p) prm->prob[p] = d[p];
-        rc = sem_solve_launch_multi(*prm, owner->num_sms, mi, s);
+        rc = sem_solve_launch_multi(*prm, mode, owner->num_sms, mi, s);
         delete prm;
     }
     if (rc) return rc;

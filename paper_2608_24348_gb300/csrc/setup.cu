@@ -317,6 +317,7 @@ extern "C" int sem_setup(int N, int nelx, int nely, int nelz, const double exten
     if (!vertices && !extents) return SEM_ERR_ARG;
     if ((int64_t)nelx * N > (1 << 30) || (int64_t)nely * N > (1 << 30) || (int64_t)nelz * N > (1 << 30))
         return SEM_ERR_ARG;
+    if (((int64_t)nely * N + 1) * ((int64_t)nelz * N + 1) >= ((int64_t)1 << 31) - 8) return SEM_ERR_ARG;
     sem_ctx *c = (sem_ctx *)calloc(1, sizeof(sem_ctx));
     if (!c) return SEM_ERR_NOMEM;
     c->N = N;

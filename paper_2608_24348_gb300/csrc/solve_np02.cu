@@ -1,7 +1,12 @@
-// solve_np02.cu -- persistent solver kernel for order N = 1 (up to 8 problems).
+// solve_np02.cu -- persistent solver kernels for order N = 1 (up to 8 problems).
 #include "solver.cuh"
 
-int sem_solve_launch_np2(const SolveParams<8> &p, int sms, long long mi, cudaStream_t s)
+int sem_solve_launch_np2(const SolveParams<8> &p, int mode, int sms, long long mi, cudaStream_t s)
 {
-    return launch_solve<8, 2>(p, sms, mi, s);
+    switch (mode) {
+        case MODE_F64: return launch_solve<8, MODE_F64, 2>(p, sms, mi, s);
+        case MODE_F32: return launch_solve<8, MODE_F32, 2>(p, sms, mi, s);
+        case MODE_TC: return launch_solve<8, MODE_TC, 2>(p, sms, mi, s);
+        default: return SEM_ERR_ARG;
+    }
 }

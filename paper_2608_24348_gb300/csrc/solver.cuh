@@ -16,18 +16,22 @@
 //   JACGS  unique  minv = 1/dssum(minv);  sum b  (mean removal when h2 == 0)
 //   AX0    element w = A x                                      (FP64)
 //   R0     unique  r = b' - dssum(w); <r,r>, <r,z>, <b',b'>      (plain PCG)
-//   A      element p = z + beta p; w = A p; <p,w>                (FP64)
-//   C      unique  x += alpha p; r -= alpha dssum(w); <r,r>, <r,z>
+//   A      element x += alpha p (previous step); p = z + beta p; w = A p; <p,w>
+//   C      unique  r -= alpha dssum(w); <r,r>, <r,z>
+//   XUPD   local   x += alpha p (the last step, after convergence)
 //   R64    unique  r = b' - dssum(w); <r,r>, <b',b'>            (refinement)
 //   INIT32 unique  r32 = r / ||r||; d = 0; <r32,r32>, <r32,z32>
-//   A32    element p32 = z32 + beta p32; w32 = A32 p32; <p32,w32>
-//   C32    unique  d += alpha p32; r32 -= alpha dssum(w32); ...
-//   UPD    local   x += ||r|| d
+//   A32    element d += alpha p32; p32 = z32 + beta p32; w32 = A32 p32; <p32,w32>
+//   C32    unique  r32 -= alpha dssum(w32); <r32,r32>, <r32,z32>
+//   UPD    local   x += ||r|| (d + alpha p32 when that last step is pending)
 //   FINAL  local   sum B x              (h2 == 0: remove the B-weighted mean)
 //   SHIFT  local   x -= sum(B x) / sum(B)
 // The inner product <a,b> = sum_local a b / mult is evaluated over unique
 // nodes, where it is a plain sum; <p, dssum(Ap)> equals sum_local p (Ap)
 // for a continuous p, which lets the element phase produce it directly.
+// Unique-node items are a chunk of 256 consecutive gx on SEM_UQ_ROWS rows
+// (gy, gz): the y/z copies are computed once per row, the x copies once per
+// thread, and all loads of a thread are issued before any store.
 #pragma once
 
 #include <type_traits>
@@ -39,10 +43,15 @@
 
 #define SEM_MAXP 64
 #define SEM_SOLVE_THREADS 256
+#define SEM_UQ_ROWS 4
+
+// Which element operators a solver kernel carries (keeps each kernel's
+// register budget to what its mode needs).
+enum SolveMode { MODE_F64 = 0, MODE_F32 = 1, MODE_TC = 2 };
 
 enum SolvePhase {
     PH_JAC = 0, PH_JACGS, PH_AX0, PH_R0, PH_A, PH_C, PH_R64, PH_INIT32, PH_A32, PH_C32, PH_UPD,
-    PH_FINAL, PH_SHIFT, PH_DONE
+    PH_FINAL, PH_SHIFT, PH_XUPD, PH_DONE
 };
 
 struct ProbDesc {
@@ -61,7 +70,7 @@ struct ProbDesc {
 };
 
 struct PState {
-    int phase, iters, outer, inner_iters, status, first, nvals, pad;
+    int phase, iters, outer, inner_iters, status, first, nvals, pending;
     double rz, alpha, beta, bnorm, rnorm, target, bmean, scale, prev_rnorm, inner_target, shift;
 };
 
@@ -115,10 +124,13 @@ __device__ __forceinline__ int phase_nvals(int ph)
 __device__ __forceinline__ int64_t phase_items(const ProbDesc &P, int ph)
 {
     switch (ph) {
-        case PH_JAC: case PH_UPD: case PH_FINAL: case PH_SHIFT:
+        case PH_JAC: case PH_UPD: case PH_FINAL: case PH_SHIFT: case PH_XUPD:
             return (P.nL + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS;
-        case PH_JACGS: case PH_R0: case PH_C: case PH_R64: case PH_INIT32: case PH_C32:
-            return (P.nG + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS;
+        case PH_JACGS: case PH_R0: case PH_C: case PH_R64: case PH_INIT32: case PH_C32: {
+            const int64_t nxch = (P.gs.ngx + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS;
+            const int64_t rows = (int64_t)P.gs.ngy * P.gs.ngz;
+            return nxch * ((rows + SEM_UQ_ROWS - 1) / SEM_UQ_ROWS);
+        }
         case PH_AX0: case PH_A:
             return (P.E + P.NE - 1) / P.NE;
         case PH_A32:
@@ -163,8 +175,8 @@ __device__ __forceinline__ void block_accumulate(double v[3], double *s_red, dou
 // kind 0: w64 = A64 x;  kind 1: FP64 p-update + w = A p + <p,w>;
 // kind 2: FP32 p32-update + w32 = A32 p32 + <p32,w32>.
 template <int NP, int KIND>
-__device__ __forceinline__ void elem_item(const ProbDesc &P, double beta, int first, int64_t g,
-                                          unsigned char *smem, double &acc)
+__device__ __forceinline__ void elem_item(const ProbDesc &P, double alpha, double beta, int first,
+                                          int64_t g, unsigned char *smem, double &acc)
 {
     using C = AxCfg<NP>;
     using T = typename std::conditional<KIND == 2, float, double>::type;
@@ -189,10 +201,14 @@ __device__ __forceinline__ void elem_item(const ProbDesc &P, double beta, int fi
         ax_element<NP, T>(load, store, geo, (T)P.h1, (T)P.h2, sD, sDT, su, svr, svs, tid, active);
     } else if (KIND == 1) {
         const double *r = P.r + off, *mi = P.minv + off;
-        double *p = P.p + off, *w = P.w + off;
+        double *p = P.p + off, *w = P.w + off, *x = P.x + off;
         auto load = [&](int q) {
             double pn = __ldcg(mi + q) * __ldcg(r + q);
-            if (!first) pn = fma(beta, __ldcg(p + q), pn);
+            if (!first) {
+                const double po = __ldcg(p + q);
+                x[q] = fma(alpha, po, __ldcg(x + q));
+                pn = fma(beta, po, pn);
+            }
             p[q] = pn;
             return (T)pn;
         };
@@ -203,11 +219,15 @@ __device__ __forceinline__ void elem_item(const ProbDesc &P, double beta, int fi
         ax_element<NP, T>(load, store, geo, (T)P.h1, (T)P.h2, sD, sDT, su, svr, svs, tid, active);
     } else {
         const float *r = P.r32 + off, *mi = P.minv32 + off;
-        float *p = P.p32 + off, *w = P.w32 + off;
-        const float b32 = (float)beta;
+        float *p = P.p32 + off, *w = P.w32 + off, *d = P.d32 + off;
+        const float b32 = (float)beta, a32 = (float)alpha;
         auto load = [&](int q) {
             float pn = __ldcg(mi + q) * __ldcg(r + q);
-            if (!first) pn = fmaf(b32, __ldcg(p + q), pn);
+            if (!first) {
+                const float po = __ldcg(p + q);
+                d[q] = fmaf(a32, po, __ldcg(d + q));
+                pn = fmaf(b32, po, pn);
+            }
             p[q] = pn;
             return (T)pn;
         };
@@ -219,15 +239,36 @@ __device__ __forceinline__ void elem_item(const ProbDesc &P, double beta, int fi
     }
 }
 
+// FP64 w = A x with the low-register operator (mixed modes: once per
+// refinement step); the NE elements of group g one after another.
+template <int NP>
+__device__ __forceinline__ void elem_item_lowreg(const ProbDesc &P, int64_t g, unsigned char *smem)
+{
+    constexpr int NP3 = NP * NP * NP;
+    for (int t = 0; t < P.NE; ++t) {
+        const int64_t e = g * P.NE + t;
+        if (e >= P.E) break;  // uniform across the block
+        const double *x = P.x + e * NP3;
+        double *w = P.w + e * NP3;
+        auto load = [&](int q) { return __ldcg(x + q); };
+        auto store = [&](int q, double v, double) { w[q] = v; };
+        ax_element_lowreg<NP>(load, store, P.geo64 + e * 7 * NP3, P.h1, P.h2, P.D64, smem, true);
+    }
+}
+
 // TC inner operator (16-bit tensor-core contractions, FP32 vectors).
 template <int NP>
-__device__ __forceinline__ void elem_item_tc(const ProbDesc &P, double beta, int first, int64_t g,
-                                             int fp16, unsigned char *smem, double &acc)
+__device__ __forceinline__ void elem_item_tc(const ProbDesc &P, double alpha, double beta, int first,
+                                             int64_t g, int fp16, unsigned char *smem, double &acc)
 {
-    const float b32 = (float)beta;
+    const float b32 = (float)beta, a32 = (float)alpha;
     auto load = [&](int64_t q) {
         float pn = __ldcg(P.minv32 + q) * __ldcg(P.r32 + q);
-        if (!first) pn = fmaf(b32, __ldcg(P.p32 + q), pn);
+        if (!first) {
+            const float po = __ldcg(P.p32 + q);
+            P.d32[q] = fmaf(a32, po, __ldcg(P.d32 + q));
+            pn = fmaf(b32, po, pn);
+        }
         P.p32[q] = pn;
         return pn;
     };
@@ -238,38 +279,44 @@ __device__ __forceinline__ void elem_item_tc(const ProbDesc &P, double beta, int
     ax_tc_group<NP>(load, store, P.geo32, P.D32, (float)P.h1, (float)P.h2, P.E, g, fp16, smem);
 }
 
-template <int NP>
-__device__ __forceinline__ void elem_dispatch_np(const ProbDesc &P, int ph, double beta, int first,
-                                                 int64_t g, int tc, unsigned char *smem, double &acc)
+template <int NP, int MODE>
+__device__ __forceinline__ void elem_dispatch_np(const ProbDesc &P, int ph, double alpha, double beta,
+                                                 int first, int64_t g, int tc, unsigned char *smem,
+                                                 double &acc)
 {
-    if (ph == PH_AX0)
-        elem_item<NP, 0>(P, beta, first, g, smem, acc);
-    else if (ph == PH_A)
-        elem_item<NP, 1>(P, beta, first, g, smem, acc);
-    else if (tc)
-        elem_item_tc<NP>(P, beta, first, g, tc == 2, smem, acc);
-    else
-        elem_item<NP, 2>(P, beta, first, g, smem, acc);
+    if constexpr (MODE == MODE_F64) {
+        if (ph == PH_AX0)
+            elem_item<NP, 0>(P, alpha, beta, first, g, smem, acc);
+        else
+            elem_item<NP, 1>(P, alpha, beta, first, g, smem, acc);
+    } else {
+        if (ph == PH_AX0)
+            elem_item_lowreg<NP>(P, g, smem);
+        else if constexpr (MODE == MODE_TC)
+            elem_item_tc<NP>(P, alpha, beta, first, g, tc == 2, smem, acc);
+        else
+            elem_item<NP, 2>(P, alpha, beta, first, g, smem, acc);
+    }
 }
 
-template <int... NPs>
+template <int MODE, int... NPs>
 struct ElemDispatch;
 
-template <>
-struct ElemDispatch<> {
-    __device__ static void run(const ProbDesc &, int, double, int, int64_t, int, unsigned char *,
-                               double &) {}
+template <int MODE>
+struct ElemDispatch<MODE> {
+    __device__ static void run(const ProbDesc &, int, double, double, int, int64_t, int,
+                               unsigned char *, double &) {}
 };
 
-template <int NP0, int... NPs>
-struct ElemDispatch<NP0, NPs...> {
-    __device__ static void run(const ProbDesc &P, int ph, double beta, int first, int64_t g, int tc,
-                               unsigned char *smem, double &acc)
+template <int MODE, int NP0, int... NPs>
+struct ElemDispatch<MODE, NP0, NPs...> {
+    __device__ static void run(const ProbDesc &P, int ph, double alpha, double beta, int first,
+                               int64_t g, int tc, unsigned char *smem, double &acc)
     {
         if (P.n == NP0)
-            elem_dispatch_np<NP0>(P, ph, beta, first, g, tc, smem, acc);
+            elem_dispatch_np<NP0, MODE>(P, ph, alpha, beta, first, g, tc, smem, acc);
         else
-            ElemDispatch<NPs...>::run(P, ph, beta, first, g, tc, smem, acc);
+            ElemDispatch<MODE, NPs...>::run(P, ph, alpha, beta, first, g, tc, smem, acc);
     }
 };
 
@@ -277,76 +324,174 @@ struct ElemDispatch<NP0, NPs...> {
 // unique-node and local-node items (one node per thread)
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void uniq_item(const ProbDesc &P, const PState &S, int ph, int64_t chunk,
+// y/z copies of one row (gy, gz) of unique nodes: local offsets without the x part.
+struct RowCopies {
+    int m;
+    int64_t off[4];
+};
+
+__device__ __forceinline__ void row_copies(const GsDesc &d, int row, RowCopies &R)
+{
+    const int gy = row % d.ngy, gz = row / d.ngy;
+    int ey[2], iy[2], ez[2], iz[2];
+    const int my = gs_copies_1d(gy, d.N, d.nely, d.py, ey, iy);
+    const int mz = gs_copies_1d(gz, d.N, d.nelz, d.pz, ez, iz);
+    const int64_t n3 = (int64_t)d.n * d.n * d.n;
+    R.m = 0;
+    for (int c = 0; c < mz; ++c)
+        for (int b = 0; b < my; ++b)
+            R.off[R.m++] = ((int64_t)ey[b] + (int64_t)d.nely * ez[c]) * d.nelx * n3 +
+                           (int64_t)(iz[c] * d.n + iy[b]) * d.n;
+}
+
+// Copy k (y/z part) x a (x part) of a unique node; valid when k < R.m, a < mx.
+#define UQ_FOR_COPIES(R, mx, xo, BODY)                              \
+    _Pragma("unroll") for (int k_ = 0; k_ < 4; ++k_)                \
+        _Pragma("unroll") for (int a_ = 0; a_ < 2; ++a_)            \
+            if (k_ < (R).m && a_ < (mx)) {                          \
+                const int64_t cp = (R).off[k_] + (xo)[a_];          \
+                BODY;                                               \
+            }
+
+__device__ __forceinline__ void uniq_item(const ProbDesc &P, const PState &S, int ph, int64_t item,
                                           double v[3])
 {
-    const int64_t g = chunk * SEM_SOLVE_THREADS + threadIdx.x;
-    if (g >= P.nG) return;
-    int64_t idx[8];
-    const int m = gs_copies(P.gs, g, idx);
-    const int64_t f = idx[0];
+    const GsDesc &d = P.gs;
+    const int nxch = (d.ngx + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS;
+    const int it32 = (int)item;  // unique-node items fit in 32 bits (checked at setup)
+    const int rg = it32 / nxch;
+    const int gx = (it32 - rg * nxch) * SEM_SOLVE_THREADS + threadIdx.x;
+    const int rows = d.ngy * d.ngz;
+    if (gx >= d.ngx) return;
+    const int64_t n3 = (int64_t)d.n * d.n * d.n;
+    int ex[2], ix[2];
+    const int mx = gs_copies_1d(gx, d.N, d.nelx, d.px, ex, ix);
+    const int64_t xo[2] = {ex[0] * n3 + ix[0], mx > 1 ? ex[1] * n3 + ix[1] : 0};
+    constexpr int RU = SEM_UQ_ROWS;
+    RowCopies R[RU];
+    bool ok[RU];
+#pragma unroll
+    for (int r = 0; r < RU; ++r) {
+        const int row = rg * RU + r;
+        ok[r] = row < rows;
+        if (ok[r]) row_copies(d, row, R[r]);
+        else R[r].m = 0;
+    }
     switch (ph) {
         case PH_JACGS: {
-            double s = 0.0;
-            for (int t = 0; t < m; ++t) s += __ldcg(P.minv + idx[t]);
-            const double rinv = 1.0 / s;
-            for (int t = 0; t < m; ++t) {
-                P.minv[idx[t]] = rinv;
-                if (P.minv32) P.minv32[idx[t]] = (float)rinv;
+            double s[RU], bv[RU];
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                s[r] = 0.0;
+                bv[r] = 0.0;
+                if (!ok[r]) continue;
+                UQ_FOR_COPIES(R[r], mx, xo, s[r] += __ldcg(P.minv + cp));
+                bv[r] = __ldcg(P.b + R[r].off[0] + xo[0]);
             }
-            v[0] += __ldcg(P.b + f);
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                if (!ok[r]) continue;
+                const double rinv = 1.0 / s[r];
+                UQ_FOR_COPIES(R[r], mx, xo, {
+                    P.minv[cp] = rinv;
+                    if (P.minv32) P.minv32[cp] = (float)rinv;
+                });
+                v[0] += bv[r];
+            }
         } break;
         case PH_R0:
         case PH_R64: {
-            double s = 0.0;
-            for (int t = 0; t < m; ++t) s += __ldcg(P.w + idx[t]);
-            const double bv = __ldcg(P.b + f) - S.bmean;
-            const double rv = bv - s;
-            for (int t = 0; t < m; ++t) P.r[idx[t]] = rv;
-            v[0] = fma(rv, rv, v[0]);
-            if (ph == PH_R0) {
-                v[1] = fma(rv, __ldcg(P.minv + f) * rv, v[1]);
-                v[2] = fma(bv, bv, v[2]);
-            } else {
-                v[1] = fma(bv, bv, v[1]);
+            double s[RU], bv[RU], mv[RU];
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                s[r] = 0.0;
+                bv[r] = mv[r] = 0.0;
+                if (!ok[r]) continue;
+                UQ_FOR_COPIES(R[r], mx, xo, s[r] += __ldcg(P.w + cp));
+                const int64_t f = R[r].off[0] + xo[0];
+                bv[r] = __ldcg(P.b + f) - S.bmean;
+                if (ph == PH_R0) mv[r] = __ldcg(P.minv + f);
+            }
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                if (!ok[r]) continue;
+                const double rv = bv[r] - s[r];
+                UQ_FOR_COPIES(R[r], mx, xo, P.r[cp] = rv);
+                v[0] = fma(rv, rv, v[0]);
+                if (ph == PH_R0) {
+                    v[1] = fma(rv, mv[r] * rv, v[1]);
+                    v[2] = fma(bv[r], bv[r], v[2]);
+                } else {
+                    v[1] = fma(bv[r], bv[r], v[1]);
+                }
             }
         } break;
         case PH_C: {
-            double s = 0.0;
-            for (int t = 0; t < m; ++t) s += __ldcg(P.w + idx[t]);
-            const double pv = __ldcg(P.p + f);
-            const double rv = __ldcg(P.r + f) - S.alpha * s;
-            for (int t = 0; t < m; ++t) {
-                P.r[idx[t]] = rv;
-                P.x[idx[t]] = fma(S.alpha, pv, __ldcg(P.x + idx[t]));
+            double s[RU], r0[RU], mv[RU];
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                s[r] = r0[r] = mv[r] = 0.0;
+                if (!ok[r]) continue;
+                UQ_FOR_COPIES(R[r], mx, xo, s[r] += __ldcg(P.w + cp));
+                const int64_t f = R[r].off[0] + xo[0];
+                r0[r] = __ldcg(P.r + f);
+                mv[r] = __ldcg(P.minv + f);
             }
-            v[0] = fma(rv, rv, v[0]);
-            v[1] = fma(rv, __ldcg(P.minv + f) * rv, v[1]);
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                if (!ok[r]) continue;
+                const double rv = r0[r] - S.alpha * s[r];
+                UQ_FOR_COPIES(R[r], mx, xo, P.r[cp] = rv);
+                v[0] = fma(rv, rv, v[0]);
+                v[1] = fma(rv, mv[r] * rv, v[1]);
+            }
         } break;
         case PH_INIT32: {
-            const float rv = (float)(__ldcg(P.r + f) / S.scale);
-            for (int t = 0; t < m; ++t) {
-                P.r32[idx[t]] = rv;
-                P.d32[idx[t]] = 0.0f;
+            double r0[RU];
+            float mv[RU];
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                r0[r] = 0.0;
+                mv[r] = 0.f;
+                if (!ok[r]) continue;
+                const int64_t f = R[r].off[0] + xo[0];
+                r0[r] = __ldcg(P.r + f);
+                mv[r] = __ldcg(P.minv32 + f);
             }
-            const double rd = rv;
-            v[0] = fma(rd, rd, v[0]);
-            v[1] = fma(rd, (double)(__ldcg(P.minv32 + f) * rv), v[1]);
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                if (!ok[r]) continue;
+                const float rv = (float)(r0[r] / S.scale);
+                UQ_FOR_COPIES(R[r], mx, xo, {
+                    P.r32[cp] = rv;
+                    P.d32[cp] = 0.0f;
+                });
+                const double rd = rv;
+                v[0] = fma(rd, rd, v[0]);
+                v[1] = fma(rd, (double)(mv[r] * rv), v[1]);
+            }
         } break;
         case PH_C32: {
-            float s = 0.0f;
-            for (int t = 0; t < m; ++t) s += __ldcg(P.w32 + idx[t]);
-            const float a = (float)S.alpha;
-            const float pv = __ldcg(P.p32 + f);
-            const float rv = __ldcg(P.r32 + f) - a * s;
-            const float dv = fmaf(a, pv, __ldcg(P.d32 + f));
-            for (int t = 0; t < m; ++t) {
-                P.r32[idx[t]] = rv;
-                P.d32[idx[t]] = dv;
+            float s[RU], r0[RU], mv[RU];
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                s[r] = r0[r] = mv[r] = 0.f;
+                if (!ok[r]) continue;
+                UQ_FOR_COPIES(R[r], mx, xo, s[r] += __ldcg(P.w32 + cp));
+                const int64_t f = R[r].off[0] + xo[0];
+                r0[r] = __ldcg(P.r32 + f);
+                mv[r] = __ldcg(P.minv32 + f);
             }
-            const double rd = rv;
-            v[0] = fma(rd, rd, v[0]);
-            v[1] = fma(rd, (double)(__ldcg(P.minv32 + f) * rv), v[1]);
+            const float a = (float)S.alpha;
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                if (!ok[r]) continue;
+                const float rv = r0[r] - a * s[r];
+                UQ_FOR_COPIES(R[r], mx, xo, P.r32[cp] = rv);
+                const double rd = rv;
+                v[0] = fma(rd, rd, v[0]);
+                v[1] = fma(rd, (double)(mv[r] * rv), v[1]);
+            }
         } break;
         default: break;
     }
@@ -376,8 +521,13 @@ __device__ __forceinline__ void local_item(const ProbDesc &P, const PState &S, i
             s += 2.0 * (di * dj * g[3 * n3 + l] + di * dk * g[4 * n3 + l] + dj * dk * g[5 * n3 + l]);
             P.minv[q] = P.h1 * s + P.h2 * g[6 * n3 + l];
         } break;
-        case PH_UPD:
-            P.x[q] = fma(S.scale, (double)__ldcg(P.d32 + q), __ldcg(P.x + q));
+        case PH_UPD: {
+            float dv = __ldcg(P.d32 + q);
+            if (S.pending) dv = fmaf((float)S.alpha, __ldcg(P.p32 + q), dv);
+            P.x[q] = fma(S.scale, (double)dv, __ldcg(P.x + q));
+        } break;
+        case PH_XUPD:
+            P.x[q] = fma(S.alpha, __ldcg(P.p + q), __ldcg(P.x + q));
             break;
         case PH_FINAL:
             v[0] = fma(P.geo64[(e * 7 + 6) * n3 + l], __ldcg(P.x + q), v[0]);
@@ -400,6 +550,11 @@ __device__ void advance(const SolveParams<MAXP> &prm, const ProbDesc &P, PState 
     auto finish = [&](int status) {
         S.status = status;
         S.phase = P.singular ? PH_FINAL : PH_DONE;
+    };
+    // after a C phase the last alpha p is not yet in x
+    auto finish_pending = [&](int status) {
+        S.status = status;
+        S.phase = PH_XUPD;
     };
     switch (ph) {
         case PH_JAC: S.phase = PH_JACGS; break;
@@ -429,9 +584,9 @@ __device__ void advance(const SolveParams<MAXP> &prm, const ProbDesc &P, PState 
         case PH_C: {
             S.iters += 1;
             S.rnorm = sqrt(red[0]);
-            if (!isfinite(S.rnorm)) { finish(SEM_ERR_BREAKDOWN); break; }
-            if (S.rnorm <= S.target) { finish(SEM_OK); break; }
-            if (S.iters >= prm.maxit) { finish(SEM_ERR_NOT_CONVERGED); break; }
+            if (!isfinite(S.rnorm)) { finish_pending(SEM_ERR_BREAKDOWN); break; }
+            if (S.rnorm <= S.target) { finish_pending(SEM_OK); break; }
+            if (S.iters >= prm.maxit) { finish_pending(SEM_ERR_NOT_CONVERGED); break; }
             S.beta = red[1] / S.rz;
             S.rz = red[1];
             S.first = 0;
@@ -458,11 +613,12 @@ __device__ void advance(const SolveParams<MAXP> &prm, const ProbDesc &P, PState 
             S.first = 1;
             S.beta = 0.0;
             S.inner_iters = 0;
+            S.pending = 0;
             S.phase = (red[0] > 0.0) ? PH_A32 : PH_UPD;
             break;
         case PH_A32: {
             const double pw = red[0];
-            if (!(pw > 0.0) || !isfinite(pw)) { S.phase = PH_UPD; break; }
+            if (!(pw > 0.0) || !isfinite(pw)) { S.pending = 0; S.phase = PH_UPD; break; }
             S.alpha = S.rz / pw;
             S.phase = PH_C32;
         } break;
@@ -470,7 +626,11 @@ __device__ void advance(const SolveParams<MAXP> &prm, const ProbDesc &P, PState 
             S.iters += 1;
             S.inner_iters += 1;
             const double rn = sqrt(red[0]);
-            if (!isfinite(rn) || rn <= S.inner_target || S.iters >= prm.maxit) { S.phase = PH_UPD; break; }
+            if (!isfinite(rn) || rn <= S.inner_target || S.iters >= prm.maxit) {
+                S.pending = 1;
+                S.phase = PH_UPD;
+                break;
+            }
             S.beta = red[1] / S.rz;
             S.rz = red[1];
             S.first = 0;
@@ -479,6 +639,7 @@ __device__ void advance(const SolveParams<MAXP> &prm, const ProbDesc &P, PState 
         case PH_UPD: S.outer += 1; S.phase = PH_AX0; break;
         case PH_FINAL: S.shift = red[0] / P.volume; S.phase = PH_SHIFT; break;
         case PH_SHIFT: S.phase = PH_DONE; break;
+        case PH_XUPD: S.phase = P.singular ? PH_FINAL : PH_DONE; break;
         default: S.phase = PH_DONE; break;
     }
     S.nvals = phase_nvals(S.phase);
@@ -488,8 +649,8 @@ __device__ void advance(const SolveParams<MAXP> &prm, const ProbDesc &P, PState 
 // the persistent kernel
 // ---------------------------------------------------------------------------
 
-template <int MAXP, int... NPs>
-__global__ void __launch_bounds__(SEM_SOLVE_THREADS, 2)
+template <int MAXP, int MODE, int... NPs>
+__global__ void __launch_bounds__(SEM_SOLVE_THREADS, MODE == MODE_F32 ? 3 : 2)
     k_solve(const __grid_constant__ SolveParams<MAXP> prm)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -498,7 +659,7 @@ __global__ void __launch_bounds__(SEM_SOLVE_THREADS, 2)
     __shared__ int s_phase[MAXP];
     __shared__ long long s_offs[MAXP + 1];
     __shared__ double s_alpha[MAXP], s_beta[MAXP], s_bmean[MAXP], s_scale[MAXP], s_shift[MAXP];
-    __shared__ int s_first[MAXP];
+    __shared__ int s_first[MAXP], s_pending[MAXP];
     __shared__ int s_last, s_stop;
     __shared__ unsigned s_gen;
     const int np = prm.nprob;
@@ -531,6 +692,7 @@ __global__ void __launch_bounds__(SEM_SOLVE_THREADS, 2)
             s_scale[p] = S->scale;
             s_shift[p] = S->shift;
             s_first[p] = S->first;
+            s_pending[p] = S->pending;
             s_part[p][0] = s_part[p][1] = s_part[p][2] = 0.0;
         }
         __syncthreads();
@@ -561,9 +723,12 @@ __global__ void __launch_bounds__(SEM_SOLVE_THREADS, 2)
             S.bmean = s_bmean[p];
             S.scale = s_scale[p];
             S.shift = s_shift[p];
+            S.pending = s_pending[p];
             if (ph == PH_AX0 || ph == PH_A || ph == PH_A32) {
-                ElemDispatch<NPs...>::run(P, ph, S.beta, s_first[p], local, prm.inner_tc, smem, acc);
-            } else if (ph == PH_JAC || ph == PH_UPD || ph == PH_FINAL || ph == PH_SHIFT) {
+                ElemDispatch<MODE, NPs...>::run(P, ph, S.alpha, S.beta, s_first[p], local,
+                                                prm.inner_tc, smem, acc);
+            } else if (ph == PH_JAC || ph == PH_UPD || ph == PH_FINAL || ph == PH_SHIFT ||
+                       ph == PH_XUPD) {
                 local_item(P, S, ph, local, v);
             } else {
                 uniq_item(P, S, ph, local, v);
@@ -631,32 +796,34 @@ __global__ void __launch_bounds__(SEM_SOLVE_THREADS, 2)
     }
 }
 
-// Dynamic shared memory of the element phases of one problem order.
-template <int NP>
+constexpr size_t sem_max_sz(size_t a, size_t b) { return a > b ? a : b; }
+
+// Dynamic shared memory of the element phases of one problem order and mode.
+template <int NP, int MODE>
 constexpr size_t solve_smem_np()
 {
-    return ax_smem_bytes<NP, double>() > ax_tc_smem_bytes<NP>() ? ax_smem_bytes<NP, double>()
-                                                                 : ax_tc_smem_bytes<NP>();
+    return MODE == MODE_F64 ? ax_smem_bytes<NP, double>()
+           : MODE == MODE_F32 ? sem_max_sz(ax_smem_bytes<NP, float>(), ax_lowreg_smem_bytes<NP>())
+                              : sem_max_sz(ax_tc_smem_bytes<NP>(), ax_lowreg_smem_bytes<NP>());
 }
 
-template <int... NPs>
+template <int MODE, int... NPs>
 struct SmemMax;
-template <>
-struct SmemMax<> {
+template <int MODE>
+struct SmemMax<MODE> {
     static constexpr size_t v = 0;
 };
-template <int NP0, int... NPs>
-struct SmemMax<NP0, NPs...> {
-    static constexpr size_t v = solve_smem_np<NP0>() > SmemMax<NPs...>::v ? solve_smem_np<NP0>()
-                                                                          : SmemMax<NPs...>::v;
+template <int MODE, int NP0, int... NPs>
+struct SmemMax<MODE, NP0, NPs...> {
+    static constexpr size_t v = sem_max_sz(solve_smem_np<NP0, MODE>(), SmemMax<MODE, NPs...>::v);
 };
 
 // Host launcher (cooperative, grid sized for co-residency).
-template <int MAXP, int... NPs>
+template <int MAXP, int MODE, int... NPs>
 int launch_solve(const SolveParams<MAXP> &prm, int num_sms, long long max_items, cudaStream_t s)
 {
-    auto kern = k_solve<MAXP, NPs...>;
-    const size_t smem = SmemMax<NPs...>::v;
+    auto kern = k_solve<MAXP, MODE, NPs...>;
+    const size_t smem = SmemMax<MODE, NPs...>::v;
     static bool attr = false;
     if (!attr) {
         SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
