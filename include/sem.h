@@ -57,11 +57,17 @@ extern "C" {
 #define SEM_ERR_TOO_LARGE (-8)     /* problem larger than a fixed-size scratch area */
 
 typedef enum {
-    SEM_F64 = 0,     /* FP64 storage and arithmetic */
-    SEM_F32 = 1,     /* FP32 storage and arithmetic */
-    SEM_BF16_TC = 2, /* FP32 storage, BF16 tensor-core contractions, FP32 accumulation */
-    SEM_F16_TC = 3   /* FP32 storage, FP16 tensor-core contractions, FP32 accumulation */
+    SEM_F64 = 0,       /* FP64 storage, FP64-accurate arithmetic (see below) */
+    SEM_F32 = 1,       /* FP32 storage and arithmetic */
+    SEM_BF16_TC = 2,   /* FP32 storage, BF16 tensor-core contractions, FP32 accumulation */
+    SEM_F16_TC = 3,    /* FP32 storage, FP16 tensor-core contractions, FP32 accumulation */
+    SEM_F64_NATIVE = 4 /* FP64 storage, native FP64 FMA arithmetic */
 } sem_dtype;
+/* SEM_F64 in sem_ax evaluates the FP64 operator on the FP32 pipes with
+ * error-free transformations (float pairs, compensated sums, per-element
+ * power-of-two scaling); it meets the same FP64 accuracy bar as
+ * SEM_F64_NATIVE and is several times faster on parts whose FP64 rate is a
+ * small fraction of their FP32 rate. */
 
 typedef struct sem_ctx sem_ctx;
 typedef struct sem_tgv sem_tgv;

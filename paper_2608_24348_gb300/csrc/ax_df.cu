@@ -1,0 +1,88 @@
+// ax_df.cu -- stand-alone FP64-accurate sem_ax on the FP32 pipes (float pairs).
+#include "ax_df.cuh"
+#include "common.cuh"
+
+template <int NP>
+__global__ void __launch_bounds__(AxDfCfg<NP>::THREADS, 2)
+    k_ax_df(const double *__restrict__ u, double *__restrict__ w, const dfp *__restrict__ geo,
+            const dfp *__restrict__ D, dfp h1, dfp h2, int64_t E)
+{
+    using C = AxDfCfg<NP>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    dfp *sm = reinterpret_cast<dfp *>(smem_raw);
+    dfp *sD = sm, *sDT = sm + NP * NP;
+    int *sexp = reinterpret_cast<int *>(sm + 2 * NP * NP + (size_t)C::NE * 3 * C::NP3);
+    const int grp = threadIdx.x / C::NP2, tid = threadIdx.x - grp * C::NP2;
+    dfp *su = sm + 2 * NP * NP + (size_t)grp * 3 * C::NP3;
+    dfp *svr = su + C::NP3, *svs = svr + C::NP3;
+    ax_df_load_D<NP>(D, sD, sDT);
+    for (int64_t e0 = (int64_t)blockIdx.x * C::NE; e0 < E; e0 += (int64_t)gridDim.x * C::NE) {
+        const int64_t e = e0 + grp;
+        const bool active = e < E;
+        const int64_t off = (active ? e : 0) * C::NP3;
+        const double *ue = u + off;
+        double *we = w + off;
+        auto load = [&](int p) { return ue[p]; };
+        auto store = [&](int p, double v) { we[p] = v; };
+        ax_df_element<NP>(load, store, geo + (active ? e : 0) * 7 * C::NP3, h1, h2, sD, sDT, su, svr,
+                          svs, sexp + grp, tid, active);
+    }
+}
+
+template <int NP>
+static int launch_df(const sem_ctx *c, const double *u, double *w, double h1, double h2,
+                     cudaStream_t s)
+{
+    using C = AxDfCfg<NP>;
+    const size_t smem = ax_df_smem_bytes<NP>();
+    static bool attr = false;
+    if (!attr) {
+        SEM_CUDA(cudaFuncSetAttribute(k_ax_df<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    int per_sm = 0;
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_df<NP>, C::THREADS, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t groups = sem_ceil_div(c->E, C::NE);
+    int64_t grid = (int64_t)per_sm * c->num_sms;
+    if (grid > groups) grid = groups;
+    const float h1h = (float)h1, h2h = (float)h2;
+    const dfp H1 = {h1h, (float)(h1 - (double)h1h)}, H2 = {h2h, (float)(h2 - (double)h2h)};
+    k_ax_df<NP><<<(unsigned)grid, C::THREADS, smem, s>>>(u, w, (const dfp *)c->geodf,
+                                                        (const dfp *)c->tabdf, H1, H2, c->E);
+    SEM_CHECK_LAUNCH();
+    return SEM_OK;
+}
+
+int sem_launch_ax_df(const sem_ctx *c, const double *u, double *w, double h1, double h2,
+                     cudaStream_t s)
+{
+    SEM_DISPATCH_NP(c->n, return launch_df<NP>(c, u, w, h1, h2, s));
+    return SEM_ERR_ARG;
+}
+
+// Float-pair copy of the FP64 geometry (hi = round(g), lo = round(g - hi)).
+__global__ void k_split_geo(const double *__restrict__ g64, dfp *__restrict__ gdf, int64_t n)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double g = g64[t];
+    const float h = __double2float_rn(g);
+    gdf[t] = {h, __double2float_rn(g - (double)h)};
+}
+
+int sem_make_geo_df(sem_ctx *c)
+{
+    const int64_t n = 7 * c->nL;
+    SEM_CUDA(cudaMalloc(&c->geodf, sizeof(dfp) * n));
+    k_split_geo<<<(unsigned)sem_ceil_div(n, 256), 256>>>(c->geo64, (dfp *)c->geodf, n);
+    SEM_CHECK_LAUNCH();
+    dfp hD[SEM_NPMAX * SEM_NPMAX];
+    for (int t = 0; t < c->n * c->n; ++t) {
+        const float h = (float)c->hD[t];
+        hD[t] = {h, (float)(c->hD[t] - (double)h)};
+    }
+    SEM_CUDA(cudaMalloc(&c->tabdf, sizeof(dfp) * c->n * c->n));
+    SEM_CUDA(cudaMemcpy(c->tabdf, hD, sizeof(dfp) * c->n * c->n, cudaMemcpyHostToDevice));
+    return SEM_OK;
+}

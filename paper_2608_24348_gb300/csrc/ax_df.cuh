@@ -1,0 +1,221 @@
+// ax_df.cuh -- FP64-accurate element operator evaluated on the FP32 pipes.
+//
+// GB300 executes FP64 FMAs at 1/58 of its FP32 rate, which makes the plain FP64
+// operator ALU-bound far below the HBM roofline.  This variant keeps FP64
+// inputs and outputs and FP64-level accuracy but does its arithmetic in pairs
+// of FP32 numbers (a "double-float" hi + lo with |lo| <= ulp(hi)/2):
+//   - products are made exact with TwoProd (Dekker 1971, via FMA),
+//   - sums use TwoSum (Knuth 1969) for the leading part and collect all
+//     rounding errors in a second accumulator, which is the compensated dot
+//     product Dot2 of Ogita, Rump & Oishi (2005): the result is as accurate as
+//     if computed in twice the working precision (about 2^-48) and rounded,
+//   - before splitting, every element's input is scaled by a power of two
+//     (exact) so that its largest entry is of order one; the output is scaled
+//     back, so the FP32 exponent range never limits an FP64 input.
+// The geometric factors and D are stored as float pairs (same bytes as FP64).
+// The three intrinsics-only helpers below are never contracted or reassociated
+// by the compiler (__fmul_rn / __fadd_rn / __fsub_rn / __fmaf_rn).
+#pragma once
+
+#include <stdint.h>
+
+struct dfp {
+    float hi, lo;
+};
+
+// Compensated accumulator: s is the running sum, e gathers the rounding errors.
+struct dfacc {
+    float s, e;
+};
+
+// Biased exponent field of a double (0 for zero and subnormals).
+__device__ __forceinline__ int df_bexp(double x)
+{
+    return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// x * 2^-E as a float pair, by integer operations on the bit pattern: hi takes
+// the leading 24 significand bits, lo the remaining 29 (rounded to 24).  Parts
+// below the FP32 normal range of the scaled element are dropped (they are
+// smaller than 2^-74 relative to the element's largest entry).
+__device__ __forceinline__ dfp df_split_scaled(double x, int E)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int be = (int)((b >> 52) & 0x7ff);
+    const int e = be - 1023 - E;  // scaled value = 1.m x 2^e
+    if (be == 0 || e < -126) return {0.f, 0.f};
+    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | ((unsigned)(M >> 29) & 0x7fffffu));
+    float lo = 0.f;
+    if (e >= -74) {
+        lo = __uint2float_rn((unsigned)(M & 0x1FFFFFFFull)) * __uint_as_float((unsigned)(e - 52 + 127) << 23);
+        lo = __uint_as_float(__float_as_uint(lo) | sign);
+    }
+    return {hi, lo};
+}
+
+// Exact FP32 -> FP64 widening of a normal float (zero and subnormals -> 0).
+__device__ __forceinline__ double df_widen(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xff;
+    if (ex == 0) return 0.0;
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                                 ((unsigned long long)(ex - 127 + 1023) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+// (hi + lo) * 2^E in FP64: one FP64 addition, the scaling on the exponent field.
+__device__ __forceinline__ double df_join_scaled(dfp a, int E)
+{
+    const double r = df_widen(a.hi) + df_widen(a.lo);
+    long long b = __double_as_longlong(r);
+    const int be = (int)((b >> 52) & 0x7ff);
+    if (be == 0) return 0.0;
+    const int nb = be + E;
+    if (nb <= 0) return 0.0;
+    if (nb >= 0x7ff) return __longlong_as_double((b & (1ll << 63)) | (0x7ffll << 52));
+    return __longlong_as_double(b + ((long long)E << 52));
+}
+
+// A += a * b   (a, b float pairs)
+__device__ __forceinline__ void df_mad(dfacc &A, dfp a, dfp b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float err = __fmaf_rn(a.hi, b.hi, -p);     // exact low part of a.hi * b.hi
+    err = __fmaf_rn(a.hi, b.lo, err);
+    err = __fmaf_rn(a.lo, b.hi, err);
+    const float s = __fadd_rn(A.s, p);        // TwoSum(A.s, p)
+    const float bv = __fsub_rn(s, A.s);
+    const float t = __fadd_rn(__fsub_rn(A.s, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+    A.s = s;
+    A.e = __fadd_rn(A.e, __fadd_rn(t, err));
+}
+
+// A += a   (a float pair)
+__device__ __forceinline__ void df_add(dfacc &A, dfp a)
+{
+    const float s = __fadd_rn(A.s, a.hi);
+    const float bv = __fsub_rn(s, A.s);
+    const float t = __fadd_rn(__fsub_rn(A.s, __fsub_rn(s, bv)), __fsub_rn(a.hi, bv));
+    A.s = s;
+    A.e = __fadd_rn(A.e, __fadd_rn(t, a.lo));
+}
+
+// Normalised pair of the accumulator (FastTwoSum).
+__device__ __forceinline__ dfp df_fin(dfacc A)
+{
+    const float h = __fadd_rn(A.s, A.e);
+    const float l = __fsub_rn(A.e, __fsub_rn(h, A.s));
+    return {h, l};
+}
+
+template <int NP>
+struct AxDfCfg {
+    static constexpr int NP2 = NP * NP, NP3 = NP2 * NP;
+    static constexpr int NE = (256 / NP2) > 0 ? (256 / NP2) : 1;
+    static constexpr int THREADS = NE * NP2;
+};
+
+// sD, sDT: float pairs of D and D^T; per element three pair slabs + an exponent.
+template <int NP>
+__host__ __device__ constexpr size_t ax_df_smem_bytes()
+{
+    return sizeof(dfp) * (2 * NP * NP + (size_t)AxDfCfg<NP>::NE * 3 * NP * NP * NP) +
+           sizeof(int) * AxDfCfg<NP>::NE;
+}
+
+template <int NP>
+__device__ __forceinline__ void ax_df_load_D(const dfp *__restrict__ D, dfp *sD, dfp *sDT)
+{
+    for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) {
+        const int a = t / NP, b = t - a * NP;
+        const dfp v = D[t];
+        sD[t] = v;
+        sDT[b * NP + a] = v;
+    }
+}
+
+// One element on NP*NP threads (thread (i, j) owns column u[.][j][i]).
+// load(p) -> double, store(p, double w).  All threads of the block call it.
+template <int NP, class Load, class Store>
+__device__ __forceinline__ void ax_df_element(const Load &load, const Store &store,
+                                              const dfp *__restrict__ geo, dfp h1, dfp h2,
+                                              const dfp *__restrict__ sD, const dfp *__restrict__ sDT,
+                                              dfp *__restrict__ su, dfp *__restrict__ svr,
+                                              dfp *__restrict__ svs, int *sexp, int tid, bool active)
+{
+    constexpr int NP2 = NP * NP, NP3 = NP2 * NP;
+    const int i = tid % NP, j = tid / NP;
+    double xu[NP];
+    if (tid == 0) *sexp = 0;
+    __syncthreads();
+    if (active) {
+        int m = 0;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            xu[k] = load(k * NP2 + tid);
+            m = max(m, df_bexp(xu[k]));
+        }
+        atomicMax(sexp, m);
+    }
+    __syncthreads();
+    const int E = *sexp > 0 ? *sexp - 1023 : 0;  // element scale 2^E (exact)
+    dfp ru[NP], rvt[NP], rw[NP];
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            ru[k] = df_split_scaled(xu[k], E);
+            su[k * NP2 + tid] = ru[k];
+        }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            dfacc ar = {0.f, 0.f}, as = {0.f, 0.f}, at = {0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l < NP; ++l) {
+                df_mad(ar, sDT[l * NP + i], su[k * NP2 + j * NP + l]);
+                df_mad(as, sDT[l * NP + j], su[k * NP2 + l * NP + i]);
+                df_mad(at, sDT[l * NP + k], ru[l]);
+            }
+            const dfp ur = df_fin(ar), us = df_fin(as), ut = df_fin(at);
+            const int p = k * NP2 + tid;
+            const dfp g11 = geo[0 * NP3 + p], g22 = geo[1 * NP3 + p], g33 = geo[2 * NP3 + p];
+            const dfp g12 = geo[3 * NP3 + p], g13 = geo[4 * NP3 + p], g23 = geo[5 * NP3 + p];
+            const dfp bm = geo[6 * NP3 + p];
+            dfacc vr = {0.f, 0.f}, vs = {0.f, 0.f}, vt = {0.f, 0.f}, vw = {0.f, 0.f};
+            df_mad(vr, g11, ur); df_mad(vr, g12, us); df_mad(vr, g13, ut);
+            df_mad(vs, g12, ur); df_mad(vs, g22, us); df_mad(vs, g23, ut);
+            df_mad(vt, g13, ur); df_mad(vt, g23, us); df_mad(vt, g33, ut);
+            df_mad(vw, bm, ru[k]);
+            svr[p] = df_fin(vr);
+            svs[p] = df_fin(vs);
+            rvt[k] = df_fin(vt);
+            rw[k] = df_fin(vw);
+        }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            dfacc ar = {0.f, 0.f}, as = {0.f, 0.f}, at = {0.f, 0.f};  // three independent chains
+#pragma unroll
+            for (int l = 0; l < NP; ++l) {
+                df_mad(ar, sD[l * NP + i], svr[k * NP2 + j * NP + l]);
+                df_mad(as, sD[l * NP + j], svs[k * NP2 + l * NP + i]);
+                df_mad(at, sD[l * NP + k], rvt[l]);
+            }
+            df_add(ar, df_fin(as));
+            df_add(ar, df_fin(at));
+            dfacc o = {0.f, 0.f};
+            df_mad(o, h1, df_fin(ar));
+            df_mad(o, h2, rw[k]);
+            store(k * NP2 + tid, df_join_scaled(df_fin(o), E));
+        }
+    }
+    __syncthreads();
+}

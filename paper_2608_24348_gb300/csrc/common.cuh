@@ -51,6 +51,8 @@ struct sem_ctx {
     // geometry, element-blocked [E][7][n^3]: G11 G22 G33 G12 G13 G23 B
     double *geo64;
     float *geo32;
+    void *geodf;       // float pairs of geo64 (FP64-accurate operator on FP32 pipes)
+    void *tabdf;       // float pairs of D
     double *vert;      // device vertex grid [(nelz+1)(nely+1)(nelx+1)][3]
     double *jinv64;    // [E][9][n^3] dr_a/dx_c at a*3+c (allocated by the stepper)
     float *jinv32;

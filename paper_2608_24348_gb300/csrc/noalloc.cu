@@ -154,7 +154,8 @@ extern "C" int sem_pcg_solve_noalloc(int N, int nelx, int nely, int nelz, const 
     sem_solve_opts o;
     sem_solve_opts_default(&o);
     if (opts) o = *opts;
-    if (o.inner != SEM_F64 || !(o.tol >= 0) || o.maxit < 0) return SEM_ERR_ARG;
+    if ((o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE) || !(o.tol >= 0) || o.maxit < 0)
+        return SEM_ERR_ARG;
     if (!(h1 >= 0) || !(h2 >= 0) || (h1 == 0 && h2 == 0)) return SEM_ERR_ARG;
     const int n = N + 1;
     const int64_t E = (int64_t)nelx * nely * nelz;
@@ -232,7 +233,7 @@ extern "C" int sem_pcg_solve_noalloc(int N, int nelx, int nely, int nelz, const 
 
     // the array keeps the previous call's contents: the solver state must start at zero
     SEM_CUDA(cudaMemsetAsync(state, 0, sizeof(NaStateHost), s));
-    rc = k_noalloc_launch[n](prm, MODE_F64, sms, (nL + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS, s);
+    rc = k_noalloc_launch[n](prm, MODE_F64N, sms, (nL + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS, s);
     if (rc) return rc;
     NaStateHost h;
     SEM_CUDA(cudaMemcpyAsync(&h, state, sizeof(NaStateHost), cudaMemcpyDeviceToHost, s));

@@ -8,6 +8,8 @@ int sem_launch_ax_f64(const sem_ctx *c, const double *u, double *w, double h1, d
                       cudaStream_t s);  // ax_f64.cu
 int sem_launch_ax_f32(const sem_ctx *c, const float *u, float *w, float h1, float h2,
                       cudaStream_t s);  // ax_f32.cu
+int sem_launch_ax_df(const sem_ctx *c, const double *u, double *w, double h1, double h2,
+                     cudaStream_t s);   // ax_df.cu
 
 GsDesc sem_gs_desc(const sem_ctx *c)
 {
@@ -26,6 +28,8 @@ int sem_ax_dev(sem_ctx *c, const void *u, void *w, double h1, double h2, sem_dty
 {
     if (c->E == 0) return SEM_OK;
     if (dt == SEM_F64) {
+        return sem_launch_ax_df(c, (const double *)u, (double *)w, h1, h2, s);
+    } else if (dt == SEM_F64_NATIVE) {
         return sem_launch_ax_f64(c, (const double *)u, (double *)w, h1, h2, s);
     } else if (dt == SEM_F32) {
         return sem_launch_ax_f32(c, (const float *)u, (float *)w, (float)h1, (float)h2, s);
@@ -39,9 +43,10 @@ extern "C" int sem_ax(sem_ctx *c, const void *u, void *w, double h1, double h2, 
                       void *stream)
 {
     if (!c || !u || !w) return SEM_ERR_ARG;
-    if (dt < SEM_F64 || dt > SEM_F16_TC) return SEM_ERR_ARG;
+    if (dt < SEM_F64 || dt > SEM_F64_NATIVE) return SEM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    size_t bytes = (size_t)c->nL * (dt == SEM_F64 ? sizeof(double) : sizeof(float));
+    const bool f64 = dt == SEM_F64 || dt == SEM_F64_NATIVE;
+    size_t bytes = (size_t)c->nL * (f64 ? sizeof(double) : sizeof(float));
     const void *ud;
     void *wd;
     int uh, wh;

@@ -72,8 +72,10 @@ static void fill_desc(const sem_ctx *c, const sem_ws &ws, const double *b, doubl
     d.h2 = h2;
     d.geo64 = c->geo64;
     d.geo32 = c->geo32;
+    d.geodf = (const dfp *)c->geodf;
     d.D64 = c->tab64 + 2 * c->n;
     d.D32 = c->tab32 + 2 * c->n;
+    d.Ddf = (const dfp *)c->tabdf;
     d.b = b;
     d.x = x;
     d.r = ws.r;
@@ -93,7 +95,7 @@ template <int MAXP>
 static void fill_common(SolveParams<MAXP> &p, sem_ctx *owner, const sem_solve_opts &o, int nprob)
 {
     p.nprob = nprob;
-    p.mixed = o.inner != SEM_F64;
+    p.mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
     p.inner_tc = o.inner == SEM_BF16_TC ? 1 : (o.inner == SEM_F16_TC ? 2 : 0);
     p.abs_tol = o.abs_tol;
     p.maxit = o.maxit;
@@ -122,8 +124,9 @@ static long long max_items(const ProbDesc *d, int np)
 static int validate_opts(const sem_solve_opts &o)
 {
     if (!(o.tol >= 0) || o.maxit < 0 || o.max_outer < 0) return SEM_ERR_ARG;
-    if (o.inner < SEM_F64 || o.inner > SEM_F16_TC) return SEM_ERR_ARG;
-    if (o.inner != SEM_F64 && !(o.inner_tol > 0 && o.inner_tol < 1)) return SEM_ERR_ARG;
+    if (o.inner < SEM_F64 || o.inner > SEM_F64_NATIVE) return SEM_ERR_ARG;
+    const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
+    if (mixed && !(o.inner_tol > 0 && o.inner_tol < 1)) return SEM_ERR_ARG;
     return SEM_OK;
 }
 
@@ -133,7 +136,9 @@ static int enqueue(sem_ctx *owner, const sem_solve_opts &o, const ProbDesc *d, i
 {
     SEM_CUDA(cudaMemsetAsync(owner->solve_dev, 0, sizeof(SolveStateHost), s));
     const long long mi = max_items(d, np);
-    const int mode = o.inner == SEM_F64 ? MODE_F64 : (o.inner == SEM_F32 ? MODE_F32 : MODE_TC);
+    const int mode = o.inner == SEM_F64 ? MODE_F64
+                     : o.inner == SEM_F64_NATIVE ? MODE_F64N
+                     : o.inner == SEM_F32 ? MODE_F32 : MODE_TC;
     bool same = true;
     for (int p = 1; p < np; ++p) same &= (d[p].n == d[0].n);
     int rc;
@@ -178,7 +183,7 @@ extern "C" int sem_last_solve_info(sem_ctx *c, sem_solve_info *info)
 int sem_pcg_solve_dev(sem_ctx *c, int slot, const double *b, double *x, double h1, double h2,
                       const sem_solve_opts &o, cudaStream_t s)
 {
-    const bool mixed = o.inner != SEM_F64;
+    const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
     const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC;
     if (tc && c->n > 10) return SEM_ERR_ARG;
     ProbDesc d;
@@ -191,7 +196,7 @@ int sem_pcg_solve_dev_batch(sem_ctx *c, int np, const double *const *b, double *
                             double h2, const sem_solve_opts &o, cudaStream_t s)
 {
     if (np < 1 || np > 8 || np > c->nws) return SEM_ERR_ARG;
-    const bool mixed = o.inner != SEM_F64;
+    const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
     const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC;
     if (tc && c->n > 10) return SEM_ERR_ARG;
     ProbDesc d[8];
@@ -256,7 +261,7 @@ extern "C" int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const doub
     if (opts) o = *opts;
     int rc = validate_opts(o);
     if (rc) return rc;
-    const bool mixed = o.inner != SEM_F64;
+    const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
     const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<ProbDesc> d(nprob);

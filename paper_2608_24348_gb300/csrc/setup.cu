@@ -296,7 +296,7 @@ extern "C" void sem_destroy(sem_ctx *c)
 {
     if (!c) return;
     cudaDeviceSynchronize();
-    void *ps[] = {c->tab64, c->tab32, c->geo64, c->geo32, c->vert, c->jinv64, c->jinv32,
+    void *ps[] = {c->tab64, c->tab32, c->geo64, c->geo32, c->geodf, c->tabdf, c->vert, c->jinv64, c->jinv32,
                   c->solve_dev, c->partials, c->stage[0], c->stage[1]};
     for (void *p : ps)
         if (p) cudaFree(p);
@@ -306,6 +306,7 @@ extern "C" void sem_destroy(sem_ctx *c)
 }
 
 int sem_solve_state_bytes();             // pcg.cu
+int sem_make_geo_df(sem_ctx *c);         // ax_df.cu
 size_t sem_partials_bytes(int num_sms);  // pcg.cu
 
 extern "C" int sem_setup(int N, int nelx, int nely, int nelz, const double extents[3],
@@ -373,6 +374,8 @@ extern "C" int sem_setup(int N, int nelx, int nely, int nelz, const double exten
     SETUP_TRY(cudaMalloc(&c->geo64, sizeof(double) * 7 * c->nL));
     SETUP_TRY(cudaMalloc(&c->geo32, sizeof(float) * 7 * c->nL));
     rc = sem_run_geometry(c, nullptr, false, s);
+    if (rc != SEM_OK) { sem_destroy(c); return rc; }
+    rc = sem_make_geo_df(c);
     if (rc != SEM_OK) { sem_destroy(c); return rc; }
     // volume = sum of B
     {

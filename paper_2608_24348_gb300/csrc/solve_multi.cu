@@ -8,6 +8,7 @@ int sem_solve_launch_multi(const SolveParams<SEM_MAXP> &p, int mode, int sms, lo
         case MODE_F64: return launch_solve<SEM_MAXP, MODE_F64, 6, 8, 10>(p, sms, mi, s);
         case MODE_F32: return launch_solve<SEM_MAXP, MODE_F32, 6, 8, 10>(p, sms, mi, s);
         case MODE_TC: return launch_solve<SEM_MAXP, MODE_TC, 6, 8, 10>(p, sms, mi, s);
+        case MODE_F64N: return launch_solve<SEM_MAXP, MODE_F64N, 6, 8, 10>(p, sms, mi, s);
         default: return SEM_ERR_ARG;
     }
 }

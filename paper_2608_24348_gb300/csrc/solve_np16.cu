@@ -5,6 +5,7 @@ int sem_solve_launch_np16(const SolveParams<8> &p, int mode, int sms, long long 
 {
     switch (mode) {
         case MODE_F64: return launch_solve<8, MODE_F64, 16>(p, sms, mi, s);
+        case MODE_F64N: return launch_solve<8, MODE_F64N, 16>(p, sms, mi, s);
         case MODE_F32: return launch_solve<8, MODE_F32, 16>(p, sms, mi, s);
         case MODE_TC: return SEM_ERR_ARG;
         default: return SEM_ERR_ARG;

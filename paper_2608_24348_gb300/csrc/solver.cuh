@@ -37,6 +37,7 @@
 #include <type_traits>
 
 #include "ax.cuh"
+#include "ax_df.cuh"
 #include "ax_tc.cuh"
 #include "common.cuh"
 #include "gs.cuh"
@@ -44,10 +45,15 @@
 #define SEM_MAXP 64
 #define SEM_SOLVE_THREADS 256
 #define SEM_UQ_ROWS 4
+#ifndef SEM_SOLVE_F64_MINB
+#define SEM_SOLVE_F64_MINB 2
+#endif
 
 // Which element operators a solver kernel carries (keeps each kernel's
 // register budget to what its mode needs).
-enum SolveMode { MODE_F64 = 0, MODE_F32 = 1, MODE_TC = 2 };
+// MODE_F64 evaluates the FP64 operator on the FP32 pipes (float pairs,
+// ax_df.cuh); MODE_F64N uses native FP64 arithmetic.
+enum SolveMode { MODE_F64 = 0, MODE_F32 = 1, MODE_TC = 2, MODE_F64N = 3 };
 
 enum SolvePhase {
     PH_JAC = 0, PH_JACGS, PH_AX0, PH_R0, PH_A, PH_C, PH_R64, PH_INIT32, PH_A32, PH_C32, PH_UPD,
@@ -61,8 +67,10 @@ struct ProbDesc {
     double volume, h1, h2;
     const double *geo64;
     const float *geo32;
+    const dfp *geodf;
     const double *D64;
     const float *D32;
+    const dfp *Ddf;
     const double *b;
     double *x;
     double *r, *p, *w, *minv;
@@ -239,6 +247,56 @@ __device__ __forceinline__ void elem_item(const ProbDesc &P, double alpha, doubl
     }
 }
 
+// FP64-accurate element phases on the FP32 pipes (float pairs):
+// kind 0: w = A x;  kind 1: x += alpha p, p = z + beta p, w = A p, <p,w>.
+template <int NP, int KIND>
+__device__ __forceinline__ void elem_item_df(const ProbDesc &P, double alpha, double beta, int first,
+                                             int64_t g, unsigned char *smem, double &acc)
+{
+    using C = AxDfCfg<NP>;
+    dfp *sm = reinterpret_cast<dfp *>(smem);
+    dfp *sD = sm, *sDT = sm + NP * NP;
+    int *sexp = reinterpret_cast<int *>(sm + 2 * NP * NP + (size_t)C::NE * 3 * C::NP3);
+    const int grp = threadIdx.x / C::NP2;
+    const int tid = threadIdx.x - grp * C::NP2;
+    const bool inrange = grp < C::NE;
+    const int64_t e = g * C::NE + grp;
+    const bool active = inrange && e < P.E;
+    dfp *su = sm + 2 * NP * NP + (size_t)(inrange ? grp : 0) * 3 * C::NP3;
+    dfp *svr = su + C::NP3, *svs = svr + C::NP3;
+    const int64_t off = (active ? e : 0) * C::NP3;
+    const dfp *geo = P.geodf + (active ? e : 0) * 7 * C::NP3;
+    const float h1h = (float)P.h1, h2h = (float)P.h2;
+    const dfp H1 = {h1h, (float)(P.h1 - (double)h1h)}, H2 = {h2h, (float)(P.h2 - (double)h2h)};
+    ax_df_load_D<NP>(P.Ddf, sD, sDT);
+    int *myexp = sexp + (inrange ? grp : 0);
+    if (KIND == 0) {
+        const double *x = P.x + off;
+        double *w = P.w + off;
+        auto load = [&](int q) { return __ldcg(x + q); };
+        auto store = [&](int q, double v) { w[q] = v; };
+        ax_df_element<NP>(load, store, geo, H1, H2, sD, sDT, su, svr, svs, myexp, tid, active);
+    } else {
+        const double *r = P.r + off, *mi = P.minv + off;
+        double *p = P.p + off, *w = P.w + off, *x = P.x + off;
+        auto load = [&](int q) {
+            double pn = __ldcg(mi + q) * __ldcg(r + q);
+            if (!first) {
+                const double po = __ldcg(p + q);
+                x[q] = fma(alpha, po, __ldcg(x + q));
+                pn = fma(beta, po, pn);
+            }
+            p[q] = pn;
+            return pn;
+        };
+        auto store = [&](int q, double v) {
+            w[q] = v;
+            acc = fma(__ldcg(p + q), v, acc);
+        };
+        ax_df_element<NP>(load, store, geo, H1, H2, sD, sDT, su, svr, svs, myexp, tid, active);
+    }
+}
+
 // FP64 w = A x with the low-register operator (mixed modes: once per
 // refinement step); the NE elements of group g one after another.
 template <int NP>
@@ -285,6 +343,11 @@ __device__ __forceinline__ void elem_dispatch_np(const ProbDesc &P, int ph, doub
                                                  double &acc)
 {
     if constexpr (MODE == MODE_F64) {
+        if (ph == PH_AX0)
+            elem_item_df<NP, 0>(P, alpha, beta, first, g, smem, acc);
+        else
+            elem_item_df<NP, 1>(P, alpha, beta, first, g, smem, acc);
+    } else if constexpr (MODE == MODE_F64N) {
         if (ph == PH_AX0)
             elem_item<NP, 0>(P, alpha, beta, first, g, smem, acc);
         else
@@ -650,7 +713,7 @@ __device__ void advance(const SolveParams<MAXP> &prm, const ProbDesc &P, PState 
 // ---------------------------------------------------------------------------
 
 template <int MAXP, int MODE, int... NPs>
-__global__ void __launch_bounds__(SEM_SOLVE_THREADS, MODE == MODE_F32 ? 3 : 2)
+__global__ void __launch_bounds__(SEM_SOLVE_THREADS, MODE == MODE_F32 ? 3 : SEM_SOLVE_F64_MINB)
     k_solve(const __grid_constant__ SolveParams<MAXP> prm)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -802,7 +865,8 @@ constexpr size_t sem_max_sz(size_t a, size_t b) { return a > b ? a : b; }
 template <int NP, int MODE>
 constexpr size_t solve_smem_np()
 {
-    return MODE == MODE_F64 ? ax_smem_bytes<NP, double>()
+    return MODE == MODE_F64N ? ax_smem_bytes<NP, double>()
+           : MODE == MODE_F64 ? ax_df_smem_bytes<NP>()
            : MODE == MODE_F32 ? sem_max_sz(ax_smem_bytes<NP, float>(), ax_lowreg_smem_bytes<NP>())
                               : sem_max_sz(ax_tc_smem_bytes<NP>(), ax_lowreg_smem_bytes<NP>());
 }
