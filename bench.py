@@ -5,9 +5,10 @@ One step = one application of the Helmholtz operator sem_ax to the 16.8M-node
 deformed mesh (32^3 elements, N=7, interior vertices perturbed by up to 10%,
 u uniform in [-1,1] per unique node, h1 = 0.01, h2 = 1/dt with dt = 1e-3).
 The primary value is the FP64 operator's throughput in GDOF/s (local nodes
-per second); the FP32 operator, the FP64 and mixed-precision PCG solves of
-the pressure-Poisson workload and an end-to-end (host buffers) figure are
-reported beside it.  Inputs (u 134 MB, geometry 940 MB) exceed the 129 MB L2,
+per second) with the library's default FP64 path (FP64-accurate arithmetic on
+the FP32 pipes).  Beside it: native-FP64, FP32 and BF16/FP16 tensor-core
+operators, the FP64 and mixed-precision PCG solves of the pressure-Poisson
+workload and an end-to-end (host buffers) figure.  Inputs (u 134 MB, geometry 940 MB) exceed the 129 MB L2,
 so no flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -32,7 +33,15 @@ METRIC = "sem_ax GDOF/s & PCG solve ms at N=7, 32^3 elems: mixed vs FP64, 1 GB30
 # algorithmic bytes per local node of one operator application
 BYTES_F64 = 72  # read u 8 + G 48 + B 8, write w 8
 BYTES_F32 = 36
-FLOPS_PER_NODE = 12 * (N_ORDER + 1) + 21
+FLOPS_PER_NODE = 12 * (N_ORDER + 1) + 21  # FP64 flops of one operator application per node
+# FP32-pipe operations per node of the FP64-accurate operator at N=7: 60
+# compensated multiply-adds of 12 ops, 11 normalisations of 2, 2 pair additions
+# of 8, 4 for the split (profiles/sem_ax_df_24cubed_N7.md: 771 measured)
+DF_OPS_PER_NODE = 60 * 12 + 11 * 2 + 2 * 8 + 4
+# DRAM bytes per local node of k_ax_df<8> from the ncu capture on the 24^3 mesh
+# (453.2 MB read + 49.5 MB written for 7,077,888 nodes), scaled to the 32^3 mesh
+DF_TRAFFIC_PER_NODE = (453.170944e6 + 49.525248e6) / 7077888
+FP64_PROBE_TFLOPS = 1.26  # FP64 FMA rate measured on this GPU model (probe: 2.2 FMA/clk/SM)
 
 
 def peaks():
@@ -181,7 +190,7 @@ def time_kernel(fn, steps, warmup, stream, ws):
     return per, total
 
 
-def pcg_section(ctx, sem, inputs, stream, ws, reps=2):
+def pcg_section(ctx, sem, inputs, stream, ws, reps=1):
     """Pressure Poisson on the same mesh: RHS = div of a seeded random smooth
     field (|k| <= 8); FP64 Jacobi-PCG vs FP32-inner / FP64 refinement, both to
     the FP64 relative residual 1e-10.  Each solve is one persistent launch,
@@ -199,7 +208,8 @@ def pcg_section(ctx, sem, inputs, stream, ws, reps=2):
     out = {"workload": "pressure Poisson, 32^3 N=7 deformed, RHS div of random smooth field "
                        "|k|<=8, h1=1 h2=0, rel tol 1e-10"}
     sp = stream.cuda_stream
-    for name, kw in (("fp64", {}), ("mixed_f32", {"inner": "f32", "inner_tol": 1e-4}),
+    for name, kw in (("fp64", {}), ("fp64_native", {"inner": "f64_native"}),
+                     ("mixed_f32", {"inner": "f32", "inner_tol": 1e-4}),
                      ("mixed_bf16_tc", {"inner": "bf16_tc", "inner_tol": 1e-2})):
         best = None
         info = None
@@ -217,17 +227,16 @@ def pcg_section(ctx, sem, inputs, stream, ws, reps=2):
         out[name] = {"ms": barrier_max(best, ws), "iters": info["iters"],
                      "outer": info["outer_iters"], "status": info["status"],
                      "relres": info["rnorm"] / info["bnorm"] if info["bnorm"] else None}
-    if out["fp64"]["ms"] and out["mixed_f32"]["ms"]:
-        out["speedup_mixed_f32"] = out["fp64"]["ms"] / out["mixed_f32"]["ms"]
-        out["speedup_mixed_bf16_tc"] = out["fp64"]["ms"] / out["mixed_bf16_tc"]["ms"]
+    out["speedup_mixed_f32_vs_fp64"] = out["fp64"]["ms"] / out["mixed_f32"]["ms"]
+    out["speedup_mixed_f32_vs_fp64_native"] = out["fp64_native"]["ms"] / out["mixed_f32"]["ms"]
     return out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     args = ap.parse_args()
     if args.warmup < 3:
@@ -235,7 +244,6 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
 
-    import numpy as np
     import torch
 
     ws, rank, local = dist_env()
@@ -247,6 +255,7 @@ def main():
 
     dev = torch.device("cuda", local)
     pk = peaks()
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     v = inputs.box_vertices(NEL, (2 * math.pi,) * 3, perturb=PERTURB)
     ctx = sem.Ctx(N_ORDER, NEL, (2 * math.pi,) * 3, (1, 1, 1), vertices=v)
     nL = ctx.nL
@@ -258,53 +267,71 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
 
-    clocks = Clocks(local)
-    f64 = lambda: ctx.ax(u64, w64, H1, H2, "f64", stream=sp)
-    f32 = lambda: ctx.ax(u32, w32, H1, H2, "f32", stream=sp)
-    clocks.start()
-    per64, tot64 = time_kernel(f64, args.steps, args.warmup, stream, ws)
-    clk = clocks.stop()
-    per32, tot32 = time_kernel(f32, args.steps, args.warmup, stream, ws)
-    tot64 = barrier_max(tot64, ws)
-    tot32 = barrier_max(tot32, ws)
-    ms64 = tot64 / args.steps
-    ms32 = tot32 / args.steps
-    gdof64 = ws * nL / (ms64 * 1e-3) / 1e9
-    gdof32 = ws * nL / (ms32 * 1e-3) / 1e9
-    avg64 = statistics.mean(per64)
-    avg32 = statistics.mean(per32)
+    def run(dt, x, y):
+        return lambda: ctx.ax(x, y, H1, H2, dt, stream=sp)
 
-    # end to end through the C ABI with pinned host buffers
+    clocks = Clocks(local)
+    clocks.start()
+    per64, tot64 = time_kernel(run("f64", u64, w64), args.steps, args.warmup, stream, ws)
+    k2 = max(20, args.steps // 5)
+    per_nat, tot_nat = time_kernel(run("f64_native", u64, w64), k2, 3, stream, ws)
+    per32, tot32 = time_kernel(run("f32", u32, w32), args.steps, args.warmup, stream, ws)
+    per_bf, tot_bf = time_kernel(run("bf16_tc", u32, w32), k2, 3, stream, ws)
+    per_f16, tot_f16 = time_kernel(run("f16_tc", u32, w32), k2, 3, stream, ws)
+    pcg = pcg_section(ctx, sem, inputs, stream, ws)
+    clk = clocks.stop()
+
+    tot64 = barrier_max(tot64, ws)
+    ms64 = tot64 / args.steps
+    gdof = lambda ms: ws * nL / (ms * 1e-3) / 1e9
+    avg64 = statistics.mean(per64)
+    mhz = clk.get("sm_max_mhz") or pk["sm_max_mhz"]
+    fp32_peak = 128 * n_sms * mhz * 1e6 / 1e12          # FP32-pipe ops/s (T)
+    fp64_peak = FP64_PROBE_TFLOPS
+    df_ops = DF_OPS_PER_NODE * nL / (avg64 * 1e-3) / 1e12
+    avg_nat = statistics.mean(per_nat)
+    avg32 = statistics.mean(per32)
+    hbm = lambda B, ms: B * nL / (ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with pinned host buffers (H2D of u, D2H of w)
     uh = torch.from_numpy(u_h).pin_memory()
     wh = torch.empty_like(uh).pin_memory()
     ctx.ax(uh, wh, H1, H2, "f64", stream=sp)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ne = max(3, min(args.steps, 10))
+    ne = 20
     for _ in range(ne):
         ctx.ax(uh, wh, H1, H2, "f64", stream=sp)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / ne
-    e2e_s = barrier_max(e2e_s, ws)
-
-    pcg = pcg_section(ctx, sem, inputs, stream, ws)
+    e2e_s = barrier_max((time.perf_counter() - t0) / ne, ws)
 
     line = {
-        "metric": METRIC, "value": gdof64, "unit": "GDOF/s", "n_gpus": ws, "steps": args.steps,
+        "metric": METRIC, "value": gdof(ms64), "unit": "GDOF/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "sem_ax FP64, 32^3 elements N=7 deformed (16.8M local nodes), "
-                               "h1=0.01 h2=1000", "N": N_ORDER, "elements": list(NEL),
-                   "local_nodes": nL, "l2": "inputs larger than L2 (1.2 GB per application)"},
-        "roofline": {"bound": "hbm", "achieved": BYTES_F64 * nL / (avg64 * 1e-3) / 1e9,
-                     "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": BYTES_F64 * nL / (avg64 * 1e-3) / 1e9 / pk["hbm_gbs"],
-                     "traffic": None, "peak_src": pk["src"], "kernel": "k_ax<8,double>"},
-        "mixed": {"sem_ax_f32_gdofs": gdof32, "ms_per_app": ms32,
-                  "roofline": {"bound": "hbm", "achieved": BYTES_F32 * nL / (avg32 * 1e-3) / 1e9,
+        "config": {"workload": "sem_ax FP64 (FP64-accurate, FP32 pipes), 32^3 elements N=7 "
+                               "deformed (16.8M local nodes), h1=0.01 h2=1000", "N": N_ORDER,
+                   "elements": list(NEL), "local_nodes": nL,
+                   "l2": "inputs larger than L2 (1.2 GB per application), no flush"},
+        "roofline": {"bound": "alu", "achieved": df_ops, "peak": fp32_peak, "unit": "Tops/s",
+                     "frac": df_ops / fp32_peak, "traffic": DF_TRAFFIC_PER_NODE * nL,
+                     "peak_src": "128 FP32-pipe ops/clk/SM x SMs x max SM clock",
+                     "kernel": "k_ax_df<8>", "ops_per_node": DF_OPS_PER_NODE,
+                     "hbm_achieved_gbs": hbm(BYTES_F64, avg64),
+                     "hbm_frac": hbm(BYTES_F64, avg64) / pk["hbm_gbs"],
+                     "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_src": pk["src"]},
+        "native_f64": {"gdofs": gdof(barrier_max(tot_nat, ws) / k2),
+                       "roofline": {"bound": "alu", "unit": "TFLOP/s",
+                                    "achieved": FLOPS_PER_NODE * nL / (avg_nat * 1e-3) / 1e12,
+                                    "peak": fp64_peak, "peak_src": "FP64 FMA probe",
+                                    "frac": FLOPS_PER_NODE * nL / (avg_nat * 1e-3) / 1e12 / fp64_peak,
+                                    "hbm_frac": hbm(BYTES_F64, avg_nat) / pk["hbm_gbs"]}},
+        "mixed": {"sem_ax_f32_gdofs": gdof(barrier_max(tot32, ws) / args.steps),
+                  "roofline": {"bound": "hbm", "achieved": hbm(BYTES_F32, avg32),
                                "peak": pk["hbm_gbs"], "unit": "GB/s",
-                               "frac": BYTES_F32 * nL / (avg32 * 1e-3) / 1e9 / pk["hbm_gbs"]},
-                  "speedup_vs_f64": ms64 / ms32},
+                               "frac": hbm(BYTES_F32, avg32) / pk["hbm_gbs"]},
+                  "sem_ax_bf16_tc_gdofs": gdof(barrier_max(tot_bf, ws) / k2),
+                  "sem_ax_f16_tc_gdofs": gdof(barrier_max(tot_f16, ws) / k2)},
         "pcg": pcg,
         "e2e": {"value": ws * nL / e2e_s / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": 8 * nL,
                 "d2h_bytes_per_step": 8 * nL},
