@@ -108,6 +108,12 @@ SEM_API const char *sem_strerror(int code);
  * SEM_ERR_CUDA); empty if none. */
 SEM_API const char *sem_last_cuda_error(void);
 
+/* Status of the bounded device-side waits of asynchronous stand-alone kernels
+ * (the bulk-copy staged operator) since the previous call: SEM_OK, or
+ * SEM_ERR_TIMEOUT if a staged copy did not arrive in time (its output is then
+ * incomplete).  Synchronises the device; clears the status. */
+SEM_API int sem_device_status(sem_ctx *ctx);
+
 /* Node coordinates: xyz holds 3 E-vectors (x, then y, then z), FP64. */
 SEM_API int sem_coords(sem_ctx *ctx, double *xyz, void *stream);
 
@@ -124,6 +130,19 @@ SEM_API int sem_geom(sem_ctx *ctx, double *out, void *stream);
  * to 16 bits for tensor-core contractions with FP32 accumulation. */
 SEM_API int sem_ax(sem_ctx *ctx, const void *u, void *w, double h1, double h2, sem_dtype dtype,
            void *stream);
+
+/* Autotuner of sem_ax's kernel choice for the context's order N and dtype.
+ * Times every candidate tile shape (for SEM_F32: 0 = direct loads, 1 =
+ * bulk-copy staged, 256 threads x 2 stages, 2 = staged, 128 threads x 3
+ * stages; other dtypes have one candidate) reps times on the context's solver
+ * workspace (scratch between solves; no allocation), stores the fastest for
+ * this process and returns it in *best; ms (may be NULL) receives the average
+ * time of each candidate (-1 where a candidate does not apply).  Synchronous. */
+SEM_API int sem_tune_ax(sem_ctx *ctx, sem_dtype dtype, int reps, double *ms, int *best);
+
+/* Selects sem_ax's kernel for order N and dtype in this process (e.g. from a
+ * cached tuning result).  Until set, a built-in per-order default applies. */
+SEM_API int sem_set_ax_variant(int N, sem_dtype dtype, int variant);
 
 /* Direct-stiffness sum in place (Sec. 2, gather/scatter): every local copy of
  * a unique node receives the sum of all its copies (Q Q^T u).  Deterministic:

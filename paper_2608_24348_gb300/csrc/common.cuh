@@ -64,6 +64,8 @@ struct sem_ctx {
     void *solve_host;     // pinned
     void *partials;       // reduction partials (device)
     size_t partials_bytes;
+    // error word of bounded waits in stand-alone kernels (SEM_OK or SEM_ERR_TIMEOUT)
+    void *err_dev;
     // host-pointer staging
     void *stage[2];
     size_t stage_bytes;

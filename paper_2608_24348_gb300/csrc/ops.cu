@@ -6,10 +6,43 @@ int sem_ax_tc(sem_ctx *c, const float *u, float *w, double h1, double h2, int fp
               cudaStream_t s);  // ax_tc.cu
 int sem_launch_ax_f64(const sem_ctx *c, const double *u, double *w, double h1, double h2,
                       cudaStream_t s);  // ax_f64.cu
-int sem_launch_ax_f32(const sem_ctx *c, const float *u, float *w, float h1, float h2,
-                      cudaStream_t s);  // ax_f32.cu
+int sem_launch_ax_f32_variant(const sem_ctx *c, int variant, const float *u, float *w, float h1,
+                              float h2, cudaStream_t s);  // ax_f32.cu
 int sem_launch_ax_df(const sem_ctx *c, const double *u, double *w, double h1, double h2,
                      cudaStream_t s);   // ax_df.cu
+
+// ---------------------------------------------------------------------------
+// Per-order kernel choice (the tile shape of the stand-alone operator)
+// ---------------------------------------------------------------------------
+
+#define SEM_NVARIANT 3
+static int g_variant[SEM_NMAX + 1][5];  // 0 = not set -> built-in default
+static int g_variant_set[SEM_NMAX + 1][5];
+
+// Built-in defaults from measurements on GB300: staged 128 x 3 for N = 7 and
+// 9, staged 256 x 2 for N = 3 and 5, direct loads otherwise.
+static int default_variant(int N, sem_dtype dt)
+{
+    if (dt != SEM_F32) return 0;
+    if (N == 7 || N == 9) return 2;
+    if (N == 3 || N == 5) return 1;
+    return 0;
+}
+
+int sem_ax_variant(int N, sem_dtype dt)
+{
+    if (N < 1 || N > SEM_NMAX || dt < SEM_F64 || dt > SEM_F64_NATIVE) return 0;
+    return g_variant_set[N][dt] ? g_variant[N][dt] : default_variant(N, dt);
+}
+
+extern "C" int sem_set_ax_variant(int N, sem_dtype dt, int variant)
+{
+    if (N < 1 || N > SEM_NMAX || dt < SEM_F64 || dt > SEM_F64_NATIVE) return SEM_ERR_ARG;
+    if (variant < 0 || variant >= SEM_NVARIANT || (dt != SEM_F32 && variant != 0)) return SEM_ERR_ARG;
+    g_variant[N][dt] = variant;
+    g_variant_set[N][dt] = 1;
+    return SEM_OK;
+}
 
 GsDesc sem_gs_desc(const sem_ctx *c)
 {
@@ -22,6 +55,8 @@ GsDesc sem_gs_desc(const sem_ctx *c)
     return d;
 }
 
+int sem_ax_variant(int N, sem_dtype dt);
+
 // Device-pointer form (used by the stepper as well).
 int sem_ax_dev(sem_ctx *c, const void *u, void *w, double h1, double h2, sem_dtype dt,
                cudaStream_t s)
@@ -32,7 +67,8 @@ int sem_ax_dev(sem_ctx *c, const void *u, void *w, double h1, double h2, sem_dty
     } else if (dt == SEM_F64_NATIVE) {
         return sem_launch_ax_f64(c, (const double *)u, (double *)w, h1, h2, s);
     } else if (dt == SEM_F32) {
-        return sem_launch_ax_f32(c, (const float *)u, (float *)w, (float)h1, (float)h2, s);
+        return sem_launch_ax_f32_variant(c, sem_ax_variant(c->N, SEM_F32), (const float *)u, (float *)w,
+                                         (float)h1, (float)h2, s);
     } else if (dt == SEM_BF16_TC || dt == SEM_F16_TC) {
         return sem_ax_tc(c, (const float *)u, (float *)w, h1, h2, dt == SEM_F16_TC, s);
     }
@@ -185,4 +221,54 @@ extern "C" int sem_jacobi(sem_ctx *c, double h1, double h2, double *minv, void *
         SEM_CUDA(cudaStreamSynchronize(s));
     }
     return SEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the stand-alone operator's tile shape
+// ---------------------------------------------------------------------------
+
+extern "C" int sem_tune_ax(sem_ctx *c, sem_dtype dt, int reps, double *ms, int *best)
+{
+    if (!c || !best || dt < SEM_F64 || dt > SEM_F64_NATIVE) return SEM_ERR_ARG;
+    if (reps < 1) reps = 5;
+    const int nvar = dt == SEM_F32 ? SEM_NVARIANT : 1;
+    // the solver workspace of slot 0 serves as input and output (its contents
+    // are scratch between solves); u = r32, w = w32
+    const float *u = c->ws[0].r32;
+    float *w = c->ws[0].w32;
+    cudaStream_t s = 0;
+    cudaEvent_t e0, e1;
+    SEM_CUDA(cudaEventCreate(&e0));
+    SEM_CUDA(cudaEventCreate(&e1));
+    SEM_CUDA(cudaMemsetAsync((void *)u, 0, sizeof(float) * c->nL, s));
+    double best_ms = 1e300;
+    int bi = 0;
+    for (int v = 0; v < nvar; ++v) {
+        double t = 1e300;
+        int rc = SEM_OK;
+        if (dt == SEM_F32) {
+            rc = sem_launch_ax_f32_variant(c, v, u, w, 1.0f, 1.0f, s);  // warm-up
+            if (rc == SEM_OK) {
+                SEM_CUDA(cudaEventRecord(e0, s));
+                for (int k = 0; k < reps && rc == SEM_OK; ++k)
+                    rc = sem_launch_ax_f32_variant(c, v, u, w, 1.0f, 1.0f, s);
+                SEM_CUDA(cudaEventRecord(e1, s));
+                SEM_CUDA(cudaEventSynchronize(e1));
+                float f = 0.f;
+                SEM_CUDA(cudaEventElapsedTime(&f, e0, e1));
+                t = f / reps;
+            }
+        } else {
+            t = 0.0;
+        }
+        if (ms) ms[v] = rc == SEM_OK ? t : -1.0;
+        if (rc == SEM_OK && t < best_ms) {
+            best_ms = t;
+            bi = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *best = bi;
+    return sem_set_ax_variant(c->N, dt, bi);
 }

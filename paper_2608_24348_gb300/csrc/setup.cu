@@ -296,7 +296,7 @@ extern "C" void sem_destroy(sem_ctx *c)
 {
     if (!c) return;
     cudaDeviceSynchronize();
-    void *ps[] = {c->tab64, c->tab32, c->geo64, c->geo32, c->geodf, c->tabdf, c->vert, c->jinv64, c->jinv32,
+    void *ps[] = {c->tab64, c->tab32, c->geo64, c->geo32, c->geodf, c->tabdf, c->vert, c->jinv64, c->jinv32, c->err_dev,
                   c->solve_dev, c->partials, c->stage[0], c->stage[1]};
     for (void *p : ps)
         if (p) cudaFree(p);
@@ -395,11 +395,22 @@ extern "C" int sem_setup(int N, int nelx, int nely, int nelz, const double exten
     SETUP_TRY(cudaMemset(c->solve_dev, 0, sem_solve_state_bytes()));
     SETUP_TRY(cudaMallocHost(&c->solve_host, sem_solve_state_bytes()));
     SETUP_TRY(cudaMalloc(&c->partials, sem_partials_bytes(c->num_sms)));
+    SETUP_TRY(cudaMalloc(&c->err_dev, sizeof(int)));
+    SETUP_TRY(cudaMemset(c->err_dev, 0, sizeof(int)));
     memset(c->solve_host, 0, sem_solve_state_bytes());
     SETUP_TRY(cudaDeviceSynchronize());
 #undef SETUP_TRY
     *out = c;
     return SEM_OK;
+}
+
+extern "C" int sem_device_status(sem_ctx *c)
+{
+    if (!c) return SEM_ERR_ARG;
+    int h = 0;
+    SEM_CUDA(cudaMemcpy(&h, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    SEM_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
+    return h;
 }
 
 extern "C" int sem_get_info(const sem_ctx *c, sem_ctx_info *info)

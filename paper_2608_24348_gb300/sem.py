@@ -64,7 +64,7 @@ EXPORTS = ["sem_setup", "sem_destroy", "sem_get_info", "sem_strerror", "sem_coor
            "sem_ax", "sem_dssum", "sem_jacobi", "sem_solve_opts_default", "sem_pcg_solve",
            "sem_last_solve_info", "sem_pcg_solve_batched", "sem_tgv_init", "sem_tgv_set",
            "sem_tgv_step", "sem_tgv_get", "sem_tgv_energy", "sem_tgv_destroy",
-           "sem_pcg_solve_noalloc"]
+           "sem_pcg_solve_noalloc", "sem_device_status", "sem_tune_ax", "sem_set_ax_variant"]
 
 
 def lib_path() -> str:
@@ -89,6 +89,9 @@ def load(build_if_missing: bool = True):
         L.sem_destroy.argtypes = [vp]
         L.sem_destroy.restype = None
         L.sem_get_info.argtypes = [vp, ctypes.POINTER(CtxInfo)]
+        L.sem_device_status.argtypes = [vp]
+        L.sem_tune_ax.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, ip]
+        L.sem_set_ax_variant.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.sem_coords.argtypes = [vp, vp, vp]
         L.sem_geom.argtypes = [vp, vp, vp]
         L.sem_ax.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
@@ -193,6 +196,10 @@ class Ctx:
         except Exception:
             pass
 
+    def device_status(self):
+        """SEM_OK, or SEM_ERR_TIMEOUT if a bounded wait of a staged kernel gave up."""
+        return _lib.sem_device_status(self._h)
+
     # -- setup exports
     def coords(self, out, stream=None):
         _check(_lib.sem_coords(self._h, ptr(out), _sp(out, stream)), "sem_coords")
@@ -281,6 +288,43 @@ def pcg_solve_noalloc(N, nel, periodic, geom, b, x, h1=1.0, h2=0.0, stream=None,
     if rc not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT):
         _check(rc, "sem_pcg_solve_noalloc")
     return info.as_dict()
+
+
+def set_ax_variant(N, dtype, variant):
+    """Select sem_ax's kernel for order N and dtype in this process."""
+    L = load()
+    _check(L.sem_set_ax_variant(int(N), DTYPES[dtype] if isinstance(dtype, str) else int(dtype),
+                                int(variant)), "sem_set_ax_variant")
+
+
+def autotune(ctx, dtype="f32", reps=5, cache=None):
+    """Pick sem_ax's kernel for ctx's order and dtype by timing the candidates.
+
+    cache: path of a JSON file keyed by (GPU name, N, dtype); a cached choice is
+    applied without timing, a new one is written back.  Returns
+    {"variant": v, "ms": [per candidate], "cached": bool}."""
+    import json
+    import torch
+    L = load()
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    key = f"{torch.cuda.get_device_name()}|N={ctx.N}|dtype={dt}"
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+        if key in table:
+            set_ax_variant(ctx.N, dt, table[key]["variant"])
+            return dict(table[key], cached=True)
+    ms = (ctypes.c_double * 8)(*([-1.0] * 8))
+    best = ctypes.c_int()
+    _check(L.sem_tune_ax(ctx.handle, dt, int(reps), ms, ctypes.byref(best)), "sem_tune_ax")
+    out = {"variant": best.value, "ms": [ms[i] for i in range(3 if dt == F32 else 1)]}
+    if cache:
+        table[key] = out
+        os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+        with open(cache, "w") as f:
+            json.dump(table, f, indent=1)
+    return dict(out, cached=False)
 
 
 class TGV:

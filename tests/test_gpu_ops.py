@@ -72,6 +72,7 @@ def test_ax_f64_f32(sem, N, nel, perturb, h1, h2):
     wd32 = torch.empty_like(ud32)
     ctx.ax(ud32, wd32, h1, h2, "f32")
     assert rel_err(wd32.cpu().numpy().astype(np.float64), ref32) <= 1e-5
+    assert ctx.device_status() == 0  # no bounded wait of the staged kernel gave up
 
 
 @pytest.mark.parametrize("dtype,bound", [("bf16_tc", 3e-2), ("f16_tc", 4e-3)])
@@ -99,6 +100,28 @@ def test_ax_tensor_core_rejects_high_order(sem):
     u = torch.zeros(ctx.nL, dtype=torch.float32, device=dev)
     with pytest.raises(sem.SemError):
         ctx.ax(u, torch.empty_like(u), 1.0, 0.0, "bf16_tc")
+
+
+def test_autotuner_candidates_keep_parity(sem, tmp_path):
+    """Every tile-shape candidate of the FP32 operator gives the same result; the
+    tuner's choice is cached per (GPU, N, dtype) and re-applied from the cache."""
+    torch, dev = torch_dev()
+    for N, nel in ((7, (5, 4, 3)), (5, (4, 4, 5)), (4, (3, 3, 3))):
+        ctx, m, _ = make(sem, N, nel, 0.1)
+        u32 = inputs.local_uniform_field(ctx.nL, seed=3).astype(np.float32)
+        ref = m.ax(u32.astype(np.float64), 0.3, 2.0)
+        ud = torch.from_numpy(u32).to(dev)
+        for v in range(3):
+            sem.set_ax_variant(N, "f32", v)
+            wd = torch.empty_like(ud)
+            ctx.ax(ud, wd, 0.3, 2.0, "f32")
+            assert rel_err(wd.cpu().numpy().astype(np.float64), ref) <= 1e-5, (N, v)
+        cache = str(tmp_path / "tune.json")
+        r1 = sem.autotune(ctx, "f32", cache=cache)
+        assert r1["variant"] in (0, 1, 2) and not r1["cached"] and r1["ms"][0] > 0
+        r2 = sem.autotune(ctx, "f32", cache=cache)
+        assert r2["cached"] and r2["variant"] == r1["variant"]
+        assert ctx.device_status() == 0
 
 
 def test_ax_host_pointers(sem):
@@ -182,6 +205,7 @@ def test_ax_full_size_sampled(sem):
         err32 = max(err32, np.abs(w32[e] - ref32).max() / np.abs(ref32).max())
     assert err64 <= 1e-12, err64
     assert err32 <= 1e-5, err32
+    assert ctx.device_status() == 0
 
 
 def test_dssum_full_size(sem):
