@@ -249,10 +249,12 @@ typedef struct {
     int status;
 } sem_tgv_diag;
 
-/* Stepper on a periodic context.  nu: viscosity; dt: time step.  op: operator
- * precision (SEM_F64, or SEM_F32 = FP32 operators, convection and inner
- * solves with FP64 refinement, histories and diagnostics).  vel / pres:
- * solver options for the velocity Helmholtz and pressure Poisson solves. */
+/* Stepper on a periodic context (N <= 9).  nu: viscosity; dt: time step.
+ * op: SEM_F64, or SEM_F32 = FP32 dealiased convection (histories, right-hand
+ * sides, refinement residuals and diagnostics stay FP64).  vel / pres: options
+ * of the velocity Helmholtz and pressure Poisson solves (NULL = defaults: FP64
+ * PCG; with op = SEM_F32 the default pressure solve is an FP32 inner PCG inside
+ * FP64 refinement).  The solves' inner field selects their precision. */
 SEM_API int sem_tgv_init(sem_ctx *ctx, double nu, double dt, sem_dtype op, const sem_solve_opts *vel,
                  const sem_solve_opts *pres, sem_tgv **out);
 

@@ -219,3 +219,74 @@ __device__ __forceinline__ void ax_df_element(const Load &load, const Store &sto
     }
     __syncthreads();
 }
+
+// Low-register variant (one thread per node, strided; every contraction read
+// from shared memory): the FP64-accurate residual inside mixed-precision
+// refinement, where the kernel's register budget belongs to the FP32 phases.
+template <int NP>
+__host__ __device__ constexpr size_t ax_df_lowreg_smem_bytes()
+{
+    return sizeof(dfp) * (2 * NP * NP + 4 * (size_t)NP * NP * NP) + 16;
+}
+
+template <int NP, class Load, class Store>
+__device__ __forceinline__ void ax_df_element_lowreg(const Load &load, const Store &store,
+                                                     const dfp *__restrict__ geo, dfp h1, dfp h2,
+                                                     const dfp *__restrict__ D, unsigned char *smem)
+{
+    constexpr int NP2 = NP * NP, NP3 = NP2 * NP;
+    dfp *sD = reinterpret_cast<dfp *>(smem), *sDT = sD + NP2;
+    dfp *su = sDT + NP2, *svr = su + NP3, *svs = svr + NP3, *svt = svs + NP3;
+    int *sexp = reinterpret_cast<int *>(svt + NP3);
+    for (int t = threadIdx.x; t < NP2; t += blockDim.x) {
+        const int a = t / NP, b = t - a * NP;
+        sD[t] = D[t];
+        sDT[b * NP + a] = D[t];
+    }
+    if (threadIdx.x == 0) *sexp = 0;
+    __syncthreads();
+    int m = 0;
+    for (int q = threadIdx.x; q < NP3; q += blockDim.x) m = max(m, df_bexp(load(q)));
+    atomicMax(sexp, m);
+    __syncthreads();
+    const int E = *sexp > 0 ? *sexp - 1023 : 0;
+    for (int q = threadIdx.x; q < NP3; q += blockDim.x) su[q] = df_split_scaled(load(q), E);
+    __syncthreads();
+    for (int q = threadIdx.x; q < NP3; q += blockDim.x) {
+        const int i = q % NP, j = (q / NP) % NP, k = q / NP2;
+        dfacc ar = {0.f, 0.f}, as = {0.f, 0.f}, at = {0.f, 0.f};
+        for (int l = 0; l < NP; ++l) {
+            df_mad(ar, sDT[l * NP + i], su[(k * NP + j) * NP + l]);
+            df_mad(as, sDT[l * NP + j], su[(k * NP + l) * NP + i]);
+            df_mad(at, sDT[l * NP + k], su[(l * NP + j) * NP + i]);
+        }
+        const dfp ur = df_fin(ar), us = df_fin(as), ut = df_fin(at);
+        const dfp g11 = geo[0 * NP3 + q], g22 = geo[1 * NP3 + q], g33 = geo[2 * NP3 + q];
+        const dfp g12 = geo[3 * NP3 + q], g13 = geo[4 * NP3 + q], g23 = geo[5 * NP3 + q];
+        dfacc vr = {0.f, 0.f}, vs = {0.f, 0.f}, vt = {0.f, 0.f};
+        df_mad(vr, g11, ur); df_mad(vr, g12, us); df_mad(vr, g13, ut);
+        df_mad(vs, g12, ur); df_mad(vs, g22, us); df_mad(vs, g23, ut);
+        df_mad(vt, g13, ur); df_mad(vt, g23, us); df_mad(vt, g33, ut);
+        svr[q] = df_fin(vr);
+        svs[q] = df_fin(vs);
+        svt[q] = df_fin(vt);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NP3; q += blockDim.x) {
+        const int i = q % NP, j = (q / NP) % NP, k = q / NP2;
+        dfacc ar = {0.f, 0.f}, as = {0.f, 0.f}, at = {0.f, 0.f};
+        for (int l = 0; l < NP; ++l) {
+            df_mad(ar, sD[l * NP + i], svr[(k * NP + j) * NP + l]);
+            df_mad(as, sD[l * NP + j], svs[(k * NP + l) * NP + i]);
+            df_mad(at, sD[l * NP + k], svt[(l * NP + j) * NP + i]);
+        }
+        df_add(ar, df_fin(as));
+        df_add(ar, df_fin(at));
+        dfacc o = {0.f, 0.f}, bu = {0.f, 0.f};
+        df_mad(bu, geo[6 * NP3 + q], su[q]);
+        df_mad(o, h1, df_fin(ar));
+        df_mad(o, h2, df_fin(bu));
+        store(q, df_join_scaled(df_fin(o), E));
+    }
+    __syncthreads();
+}

@@ -48,6 +48,9 @@
 #ifndef SEM_SOLVE_F64_MINB
 #define SEM_SOLVE_F64_MINB 2
 #endif
+#ifndef SEM_SOLVE_F32_MINB
+#define SEM_SOLVE_F32_MINB 3
+#endif
 
 // Which element operators a solver kernel carries (keeps each kernel's
 // register budget to what its mode needs).
@@ -297,20 +300,23 @@ __device__ __forceinline__ void elem_item_df(const ProbDesc &P, double alpha, do
     }
 }
 
-// FP64 w = A x with the low-register operator (mixed modes: once per
-// refinement step); the NE elements of group g one after another.
+// FP64-accurate w = A x with the low-register float-pair operator (mixed
+// modes: the FP64 residual of each refinement step); the NE elements of
+// group g one after another.
 template <int NP>
 __device__ __forceinline__ void elem_item_lowreg(const ProbDesc &P, int64_t g, unsigned char *smem)
 {
     constexpr int NP3 = NP * NP * NP;
+    const float h1h = (float)P.h1, h2h = (float)P.h2;
+    const dfp H1 = {h1h, (float)(P.h1 - (double)h1h)}, H2 = {h2h, (float)(P.h2 - (double)h2h)};
     for (int t = 0; t < P.NE; ++t) {
         const int64_t e = g * P.NE + t;
         if (e >= P.E) break;  // uniform across the block
         const double *x = P.x + e * NP3;
         double *w = P.w + e * NP3;
         auto load = [&](int q) { return __ldcg(x + q); };
-        auto store = [&](int q, double v, double) { w[q] = v; };
-        ax_element_lowreg<NP>(load, store, P.geo64 + e * 7 * NP3, P.h1, P.h2, P.D64, smem, true);
+        auto store = [&](int q, double v) { w[q] = v; };
+        ax_df_element_lowreg<NP>(load, store, P.geodf + e * 7 * NP3, H1, H2, P.Ddf, smem);
     }
 }
 
@@ -353,9 +359,9 @@ __device__ __forceinline__ void elem_dispatch_np(const ProbDesc &P, int ph, doub
         else
             elem_item<NP, 1>(P, alpha, beta, first, g, smem, acc);
     } else {
-        if (ph == PH_AX0)
+        if (ph == PH_AX0) {
             elem_item_lowreg<NP>(P, g, smem);
-        else if constexpr (MODE == MODE_TC)
+        } else if constexpr (MODE == MODE_TC)
             elem_item_tc<NP>(P, alpha, beta, first, g, tc == 2, smem, acc);
         else
             elem_item<NP, 2>(P, alpha, beta, first, g, smem, acc);
@@ -670,15 +676,21 @@ __device__ void advance(const SolveParams<MAXP> &prm, const ProbDesc &P, PState 
             S.scale = rn;
             S.phase = PH_INIT32;
         } break;
-        case PH_INIT32:
-            S.inner_target = prm.inner_tol * sqrt(red[0]);
+        case PH_INIT32: {
+            // the inner solve needs to reduce its residual only as far as the
+            // outer target requires (with a factor 2 margin), never further
+            // than inner_tol
+            double rel = 0.5 * S.target / S.rnorm;
+            if (rel < prm.inner_tol) rel = prm.inner_tol;
+            if (rel > 0.5) rel = 0.5;
+            S.inner_target = rel * sqrt(red[0]);
             S.rz = red[1];
             S.first = 1;
             S.beta = 0.0;
             S.inner_iters = 0;
             S.pending = 0;
             S.phase = (red[0] > 0.0) ? PH_A32 : PH_UPD;
-            break;
+        } break;
         case PH_A32: {
             const double pw = red[0];
             if (!(pw > 0.0) || !isfinite(pw)) { S.pending = 0; S.phase = PH_UPD; break; }
@@ -713,7 +725,7 @@ __device__ void advance(const SolveParams<MAXP> &prm, const ProbDesc &P, PState 
 // ---------------------------------------------------------------------------
 
 template <int MAXP, int MODE, int... NPs>
-__global__ void __launch_bounds__(SEM_SOLVE_THREADS, MODE == MODE_F32 ? 3 : SEM_SOLVE_F64_MINB)
+__global__ void __launch_bounds__(SEM_SOLVE_THREADS, MODE == MODE_F32 ? SEM_SOLVE_F32_MINB : SEM_SOLVE_F64_MINB)
     k_solve(const __grid_constant__ SolveParams<MAXP> prm)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -867,8 +879,8 @@ constexpr size_t solve_smem_np()
 {
     return MODE == MODE_F64N ? ax_smem_bytes<NP, double>()
            : MODE == MODE_F64 ? ax_df_smem_bytes<NP>()
-           : MODE == MODE_F32 ? sem_max_sz(ax_smem_bytes<NP, float>(), ax_lowreg_smem_bytes<NP>())
-                              : sem_max_sz(ax_tc_smem_bytes<NP>(), ax_lowreg_smem_bytes<NP>());
+           : MODE == MODE_F32 ? sem_max_sz(ax_smem_bytes<NP, float>(), ax_df_lowreg_smem_bytes<NP>())
+                              : sem_max_sz(ax_tc_smem_bytes<NP>(), ax_df_lowreg_smem_bytes<NP>());
 }
 
 template <int MODE, int... NPs>

@@ -12,8 +12,10 @@
 //                                                   (k_tgv_vrhs + 3-problem batched PCG)
 //   6. shift histories; KE and enstrophy into a device log      (k_tgv_diag_*)
 // Histories, right-hand sides and diagnostics are FP64.  With op = SEM_F32 the
-// convective term is computed in FP32 and the solves run an FP32 inner PCG
-// inside FP64 refinement.  Steady-state steps (q = 3) are captured once into
+// convective term is computed in FP32; the solves use the precision of the
+// options passed (the default pressure options then select an FP32 inner PCG
+// inside FP64 refinement; the velocity Helmholtz solves, a few iterations per
+// step, stay FP64 unless their options ask otherwise).  Steady-state steps (q = 3) are captured once into
 // a CUDA graph and replayed.  Orders N <= 9.
 #include <math.h>
 #include <stdlib.h>
@@ -765,10 +767,7 @@ extern "C" int sem_tgv_init(sem_ctx *c, double nu, double dt, sem_dtype op, cons
     sem_solve_opts_default(&T->po);
     if (vel) T->vo = *vel;
     if (pres) T->po = *pres;
-    if (op == SEM_F32) {
-        T->vo.inner = SEM_F32;
-        T->po.inner = SEM_F32;
-    }
+    if (op == SEM_F32 && !pres) T->po.inner = SEM_F32;
     const int n = c->n;
     T->M = (3 * n + 1) / 2;
     const int64_t nL = c->nL;

@@ -334,7 +334,8 @@ class TGV:
         self.ctx = ctx
         h = ctypes.c_void_p()
         vo = vel if vel is not None else opts(tol=1e-6, abs_tol=True)
-        po = pres if pres is not None else opts(tol=1e-4, abs_tol=True)
+        po = pres if pres is not None else opts(tol=1e-4, abs_tol=True,
+                                                inner="f32" if op == "f32" else "f64")
         _check(_lib.sem_tgv_init(ctx.handle, float(nu), float(dt), DTYPES[op], ctypes.byref(vo),
                                  ctypes.byref(po), ctypes.byref(h)), "sem_tgv_init")
         self._h = h

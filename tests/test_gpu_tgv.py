@@ -32,7 +32,7 @@ def _gpu_tgv(sem, ctx, nu, dt, op="f64", tight=False):
         po = sem.opts(tol=1e-12, abs_tol=False)
     else:
         vo = sem.opts(tol=1e-6, abs_tol=True)
-        po = sem.opts(tol=1e-4, abs_tol=True)
+        po = sem.opts(tol=1e-4, abs_tol=True, inner="f32" if op == "f32" else "f64")
     return sem.TGV(ctx, nu, dt, op=op, vel=vo, pres=po)
 
 
