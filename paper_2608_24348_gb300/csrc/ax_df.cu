@@ -1,5 +1,6 @@
 // ax_df.cu -- stand-alone FP64-accurate sem_ax on the FP32 pipes (float pairs).
 #include "ax_df.cuh"
+#include "ax_dfeo.cuh"
 #include "common.cuh"
 
 template <int NP>
@@ -29,10 +30,66 @@ __global__ void __launch_bounds__(AxDfCfg<NP>::THREADS, 2)
     }
 }
 
+// Folded (even-odd) variant for even NP.
+template <int NP>
+__global__ void __launch_bounds__(AxEoCfg<NP>::THREADS, 2)
+    k_ax_dfeo(const double *__restrict__ u, double *__restrict__ w, const dfp *__restrict__ geo,
+              const dfp *__restrict__ tabs, dfp h1, dfp h2, int64_t E)
+{
+    using C = AxEoCfg<NP>;
+    constexpr int HH = (NP / 2) * (NP / 2);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    dfp *sm = reinterpret_cast<dfp *>(smem_raw);
+    dfp *stab = sm;
+    int *sexp = reinterpret_cast<int *>(sm + 4 * HH + (size_t)C::NE * 5 * C::NP3);
+    const int grp = threadIdx.x / C::NP2, tid = threadIdx.x - grp * C::NP2;
+    dfp *slab = sm + 4 * HH + (size_t)grp * 5 * C::NP3;
+    for (int t = threadIdx.x; t < 4 * HH; t += blockDim.x) stab[t] = tabs[t];
+    for (int64_t e0 = (int64_t)blockIdx.x * C::NE; e0 < E; e0 += (int64_t)gridDim.x * C::NE) {
+        const int64_t e = e0 + grp;
+        const bool active = e < E;
+        const int64_t off = (active ? e : 0) * C::NP3;
+        const double *ue = u + off;
+        double *we = w + off;
+        auto load = [&](int p) { return ue[p]; };
+        auto store = [&](int p, double v) { we[p] = v; };
+        ax_dfeo_element<NP>(load, store, geo + (active ? e : 0) * 7 * C::NP3, h1, h2, stab, slab,
+                            sexp + grp, tid, active);
+    }
+}
+
+template <int NP>
+static int launch_dfeo(const sem_ctx *c, const double *u, double *w, dfp H1, dfp H2, cudaStream_t s)
+{
+    using C = AxEoCfg<NP>;
+    const size_t smem = ax_dfeo_smem_bytes<NP>();
+    static bool attr = false;
+    if (!attr) {
+        SEM_CUDA(cudaFuncSetAttribute(k_ax_dfeo<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    int per_sm = 0;
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_dfeo<NP>, C::THREADS, smem));
+    if (per_sm < 1) return SEM_ERR_ARG;
+    int64_t groups = sem_ceil_div(c->E, C::NE);
+    int64_t grid = (int64_t)per_sm * c->num_sms;
+    if (grid > groups) grid = groups;
+    k_ax_dfeo<NP><<<(unsigned)grid, C::THREADS, smem, s>>>(u, w, (const dfp *)c->geodf,
+                                                          (const dfp *)c->tabdfeo, H1, H2, c->E);
+    SEM_CHECK_LAUNCH();
+    return SEM_OK;
+}
+
 template <int NP>
 static int launch_df(const sem_ctx *c, const double *u, double *w, double h1, double h2,
                      cudaStream_t s)
 {
+    if constexpr (AxEoCfg<NP>::OK) {
+        if (ax_dfeo_smem_bytes<NP>() <= 227 * 1024) {
+            const float a = (float)h1, b = (float)h2;
+            return launch_dfeo<NP>(c, u, w, {a, (float)(h1 - (double)a)}, {b, (float)(h2 - (double)b)}, s);
+        }
+    }
     using C = AxDfCfg<NP>;
     const size_t smem = ax_df_smem_bytes<NP>();
     static bool attr = false;
@@ -84,5 +141,12 @@ int sem_make_geo_df(sem_ctx *c)
     }
     SEM_CUDA(cudaMalloc(&c->tabdf, sizeof(dfp) * c->n * c->n));
     SEM_CUDA(cudaMemcpy(c->tabdf, hD, sizeof(dfp) * c->n * c->n, cudaMemcpyHostToDevice));
+    if (c->n % 2 == 0) {  // half tables of the folded operator
+        dfp ht[4 * (SEM_NPMAX / 2) * (SEM_NPMAX / 2)];
+        ax_dfeo_tables(c->n, c->hD, ht);
+        const size_t nb = sizeof(dfp) * 4 * (c->n / 2) * (c->n / 2);
+        SEM_CUDA(cudaMalloc(&c->tabdfeo, nb));
+        SEM_CUDA(cudaMemcpy(c->tabdfeo, ht, nb, cudaMemcpyHostToDevice));
+    }
     return SEM_OK;
 }

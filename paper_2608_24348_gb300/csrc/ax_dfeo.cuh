@@ -1,0 +1,279 @@
+// ax_dfeo.cuh -- FP64-accurate element operator with folded (even-odd) contractions.
+//
+// The GLL derivative matrix is centro-antisymmetric, D[NP-1-i][NP-1-l] = -D[i][l]
+// (also D^T).  With H = NP/2 (NP even), the even and odd parts of a line,
+//     e_l = u_l + u_{NP-1-l},   o_l = u_l - u_{NP-1-l}     (l < H),
+// and the half matrices A_il = (D_il + D_{i,NP-1-l})/2, B_il = (D_il - D_{i,NP-1-l})/2,
+// every output pair of a 1-D contraction follows from two half-length sums:
+//     a_i = sum_l A_il e_l,  b_i = sum_l B_il o_l,
+//     (Du)_i = a_i + b_i,    (Du)_{NP-1-i} = b_i - a_i          (i < H),
+// which halves the multiply-adds of all six directional contractions.  The
+// arithmetic is the float-pair compensated arithmetic of ax_df.cuh.
+//
+// Thread (i, j) of an element owns column u[.][j][i] (the t direction stays in
+// registers).  For r and s it folds one line of each direction into shared
+// memory, then computes the output pairs of H lines; results return to the
+// column owner through shared memory.  Shared memory per element: five
+// float-pair slabs of NP^3 values.
+#pragma once
+
+#include "ax_df.cuh"
+
+template <int NP>
+struct AxEoCfg {
+    static constexpr int H = NP / 2;
+    static constexpr int NP2 = NP * NP, NP3 = NP2 * NP;
+    static constexpr int NE = (256 / NP2) > 0 ? (256 / NP2) : 1;
+    static constexpr int THREADS = NE * NP2;
+    static constexpr bool OK = (NP % 2) == 0;
+};
+
+// Half tables: A, B of D (gradient) and AT, BT of D^T (transpose), H*H each.
+template <int NP>
+__host__ __device__ constexpr size_t ax_dfeo_smem_bytes()
+{
+    return sizeof(dfp) * (4 * (NP / 2) * (NP / 2) + (size_t)AxEoCfg<NP>::NE * 5 * NP * NP * NP) +
+           sizeof(int) * AxEoCfg<NP>::NE;
+}
+
+// Fold a line: e[l] = x[l] + x[NP-1-l], o[l] = x[l] - x[NP-1-l] (float pairs).
+__device__ __forceinline__ dfp df_sum2(dfp a, dfp b)
+{
+    dfacc A = {a.hi, a.lo};
+    df_add(A, b);
+    return df_fin(A);
+}
+
+__device__ __forceinline__ dfp df_neg(dfp a) { return {-a.hi, -a.lo}; }
+
+// tab: the four half tables laid out [A | B | AT | BT], each H*H row-major [i][l].
+template <int NP, class Load, class Store>
+__device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &store,
+                                                const dfp *__restrict__ geo, dfp h1, dfp h2,
+                                                const dfp *__restrict__ tab, dfp *__restrict__ slab,
+                                                int *sexp, int tid, bool active)
+{
+    constexpr int H = NP / 2, NP2 = NP * NP, NP3 = NP2 * NP, HH = H * H;
+    const dfp *tA = tab, *tB = tab + HH, *tAT = tab + 2 * HH, *tBT = tab + 3 * HH;
+    dfp *su = slab, *f1 = slab + NP3, *f2 = f1 + NP3, *g1 = f2 + NP3, *g2 = g1 + NP3;
+    const int i = tid % NP, j = tid / NP;
+    // ---- load, element exponent, split
+    double xu[NP];
+    if (tid == 0) *sexp = 0;
+    __syncthreads();
+    if (active) {
+        int m = 0;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            xu[k] = load(k * NP2 + tid);
+            m = max(m, df_bexp(xu[k]));
+        }
+        atomicMax(sexp, m);
+    }
+    __syncthreads();
+    const int E = *sexp > 0 ? *sexp - 1023 : 0;
+    dfp ru[NP];
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            ru[k] = df_split_scaled(xu[k], E);
+            su[k * NP2 + tid] = ru[k];
+        }
+    }
+    __syncthreads();
+    // ---- fold the r-line (k = j, row i) into f1 and the s-line (k = j, column i) into f2
+    if (active) {
+        const dfp *lr = su + (j * NP + i) * NP;
+        dfp *fr = f1 + (j * NP + i) * NP;
+#pragma unroll
+        for (int l = 0; l < H; ++l) {
+            const dfp a = lr[l], b = lr[NP - 1 - l];
+            fr[l] = df_sum2(a, b);
+            fr[H + l] = df_sum2(a, df_neg(b));
+        }
+#pragma unroll
+        for (int l = 0; l < H; ++l) {
+            const dfp a = su[(j * NP + l) * NP + i], b = su[(j * NP + NP - 1 - l) * NP + i];
+            f2[(j * NP + l) * NP + i] = df_sum2(a, b);
+            f2[(j * NP + H + l) * NP + i] = df_sum2(a, df_neg(b));
+        }
+    }
+    __syncthreads();
+    // ---- gradient: r pairs -> g1, s pairs -> g2, t in registers
+    dfp ut[NP];
+    if (active) {
+        const int ip = i % H, kr = (i / H) * H;
+#pragma unroll
+        for (int kk = 0; kk < H; ++kk) {
+            const int k = kr + kk;
+            const dfp *fr = f1 + (k * NP + j) * NP;
+            dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l < H; ++l) {
+                df_mad(a, tA[ip * H + l], fr[l]);
+                df_mad(b, tB[ip * H + l], fr[H + l]);
+            }
+            const dfp av = df_fin(a), bv = df_fin(b);
+            g1[(k * NP + j) * NP + ip] = df_sum2(av, bv);
+            g1[(k * NP + j) * NP + NP - 1 - ip] = df_sum2(bv, df_neg(av));
+        }
+        const int jp = j % H, ks = (j / H) * H;
+#pragma unroll
+        for (int kk = 0; kk < H; ++kk) {
+            const int k = ks + kk;
+            dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l < H; ++l) {
+                df_mad(a, tA[jp * H + l], f2[(k * NP + l) * NP + i]);
+                df_mad(b, tB[jp * H + l], f2[(k * NP + H + l) * NP + i]);
+            }
+            const dfp av = df_fin(a), bv = df_fin(b);
+            g2[(k * NP + jp) * NP + i] = df_sum2(av, bv);
+            g2[(k * NP + NP - 1 - jp) * NP + i] = df_sum2(bv, df_neg(av));
+        }
+        dfp e[H], o[H];
+#pragma unroll
+        for (int l = 0; l < H; ++l) {
+            e[l] = df_sum2(ru[l], ru[NP - 1 - l]);
+            o[l] = df_sum2(ru[l], df_neg(ru[NP - 1 - l]));
+        }
+#pragma unroll
+        for (int kp = 0; kp < H; ++kp) {
+            dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l < H; ++l) {
+                df_mad(a, tA[kp * H + l], e[l]);
+                df_mad(b, tB[kp * H + l], o[l]);
+            }
+            const dfp av = df_fin(a), bv = df_fin(b);
+            ut[kp] = df_sum2(av, bv);
+            ut[NP - 1 - kp] = df_sum2(bv, df_neg(av));
+        }
+    }
+    __syncthreads();
+    // ---- geometric factors (column owner): vr -> f1, vs -> f2, vt in registers
+    dfp rw[NP];
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int p = k * NP2 + tid;
+            const dfp ur = g1[p], us = g2[p];
+            const dfp g11 = geo[0 * NP3 + p], g22 = geo[1 * NP3 + p], g33 = geo[2 * NP3 + p];
+            const dfp g12 = geo[3 * NP3 + p], g13 = geo[4 * NP3 + p], g23 = geo[5 * NP3 + p];
+            const dfp bm = geo[6 * NP3 + p];
+            dfacc vr = {0.f, 0.f}, vs = {0.f, 0.f}, vt = {0.f, 0.f}, vw = {0.f, 0.f};
+            df_mad(vr, g11, ur); df_mad(vr, g12, us); df_mad(vr, g13, ut[k]);
+            df_mad(vs, g12, ur); df_mad(vs, g22, us); df_mad(vs, g23, ut[k]);
+            df_mad(vt, g13, ur); df_mad(vt, g23, us); df_mad(vt, g33, ut[k]);
+            df_mad(vw, bm, ru[k]);
+            f1[p] = df_fin(vr);
+            f2[p] = df_fin(vs);
+            ut[k] = df_fin(vt);  // ut now holds vt of this column
+            rw[k] = df_fin(vw);
+        }
+    }
+    __syncthreads();
+    // ---- fold vr (r-line k = j, row i) into g1, vs (s-line k = j, column i) into g2
+    if (active) {
+        const dfp *lr = f1 + (j * NP + i) * NP;
+        dfp *fr = g1 + (j * NP + i) * NP;
+#pragma unroll
+        for (int l = 0; l < H; ++l) {
+            const dfp a = lr[l], b = lr[NP - 1 - l];
+            fr[l] = df_sum2(a, b);
+            fr[H + l] = df_sum2(a, df_neg(b));
+        }
+#pragma unroll
+        for (int l = 0; l < H; ++l) {
+            const dfp a = f2[(j * NP + l) * NP + i], b = f2[(j * NP + NP - 1 - l) * NP + i];
+            g2[(j * NP + l) * NP + i] = df_sum2(a, b);
+            g2[(j * NP + H + l) * NP + i] = df_sum2(a, df_neg(b));
+        }
+    }
+    __syncthreads();
+    // ---- transpose: r pairs -> f1, s pairs -> f2, t in registers
+    dfp wt[NP];
+    if (active) {
+        const int ip = i % H, kr = (i / H) * H;
+#pragma unroll
+        for (int kk = 0; kk < H; ++kk) {
+            const int k = kr + kk;
+            const dfp *fr = g1 + (k * NP + j) * NP;
+            dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l < H; ++l) {
+                df_mad(a, tAT[ip * H + l], fr[l]);
+                df_mad(b, tBT[ip * H + l], fr[H + l]);
+            }
+            const dfp av = df_fin(a), bv = df_fin(b);
+            f1[(k * NP + j) * NP + ip] = df_sum2(av, bv);
+            f1[(k * NP + j) * NP + NP - 1 - ip] = df_sum2(bv, df_neg(av));
+        }
+        const int jp = j % H, ks = (j / H) * H;
+#pragma unroll
+        for (int kk = 0; kk < H; ++kk) {
+            const int k = ks + kk;
+            dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l < H; ++l) {
+                df_mad(a, tAT[jp * H + l], g2[(k * NP + l) * NP + i]);
+                df_mad(b, tBT[jp * H + l], g2[(k * NP + H + l) * NP + i]);
+            }
+            const dfp av = df_fin(a), bv = df_fin(b);
+            f2[(k * NP + jp) * NP + i] = df_sum2(av, bv);
+            f2[(k * NP + NP - 1 - jp) * NP + i] = df_sum2(bv, df_neg(av));
+        }
+        dfp e[H], o[H];
+#pragma unroll
+        for (int l = 0; l < H; ++l) {
+            e[l] = df_sum2(ut[l], ut[NP - 1 - l]);
+            o[l] = df_sum2(ut[l], df_neg(ut[NP - 1 - l]));
+        }
+#pragma unroll
+        for (int kp = 0; kp < H; ++kp) {
+            dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l < H; ++l) {
+                df_mad(a, tAT[kp * H + l], e[l]);
+                df_mad(b, tBT[kp * H + l], o[l]);
+            }
+            const dfp av = df_fin(a), bv = df_fin(b);
+            wt[kp] = df_sum2(av, bv);
+            wt[NP - 1 - kp] = df_sum2(bv, df_neg(av));
+        }
+    }
+    __syncthreads();
+    // ---- sum of the three directions, h1 / h2 weights, rounding to FP64
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int p = k * NP2 + tid;
+            dfacc s = {wt[k].hi, wt[k].lo};
+            df_add(s, f1[p]);
+            df_add(s, f2[p]);
+            dfacc o = {0.f, 0.f};
+            df_mad(o, h1, df_fin(s));
+            df_mad(o, h2, rw[k]);
+            store(p, df_join_scaled(df_fin(o), E));
+        }
+    }
+    __syncthreads();
+}
+
+// Host: the four half tables from the FP64 derivative matrix D (row-major n x n).
+static inline void ax_dfeo_tables(int n, const double *D, dfp *out)
+{
+    const int H = n / 2, HH = H * H;
+    for (int i = 0; i < H; ++i)
+        for (int l = 0; l < H; ++l) {
+            const double a = 0.5 * (D[i * n + l] + D[i * n + n - 1 - l]);
+            const double b = 0.5 * (D[i * n + l] - D[i * n + n - 1 - l]);
+            const double at = 0.5 * (D[l * n + i] + D[(n - 1 - l) * n + i]);
+            const double bt = 0.5 * (D[l * n + i] - D[(n - 1 - l) * n + i]);
+            const double v[4] = {a, b, at, bt};
+            for (int t = 0; t < 4; ++t) {
+                const float h = (float)v[t];
+                out[t * HH + i * H + l] = {h, (float)(v[t] - (double)h)};
+            }
+        }
+}

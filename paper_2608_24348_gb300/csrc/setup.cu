@@ -296,7 +296,7 @@ extern "C" void sem_destroy(sem_ctx *c)
 {
     if (!c) return;
     cudaDeviceSynchronize();
-    void *ps[] = {c->tab64, c->tab32, c->geo64, c->geo32, c->geodf, c->tabdf, c->vert, c->jinv64, c->jinv32, c->err_dev,
+    void *ps[] = {c->tab64, c->tab32, c->geo64, c->geo32, c->geodf, c->tabdf, c->tabdfeo, c->vert, c->jinv64, c->jinv32, c->err_dev,
                   c->solve_dev, c->partials, c->stage[0], c->stage[1]};
     for (void *p : ps)
         if (p) cudaFree(p);
