@@ -34,13 +34,16 @@ METRIC = "sem_ax GDOF/s & PCG solve ms at N=7, 32^3 elems: mixed vs FP64, 1 GB30
 BYTES_F64 = 72  # read u 8 + G 48 + B 8, write w 8
 BYTES_F32 = 36
 FLOPS_PER_NODE = 12 * (N_ORDER + 1) + 21  # FP64 flops of one operator application per node
-# FP32-pipe operations per node of the FP64-accurate operator at N=7: 60
-# compensated multiply-adds of 12 ops, 11 normalisations of 2, 2 pair additions
-# of 8, 4 for the split (profiles/sem_ax_df_24cubed_N7.md: 771 measured)
-DF_OPS_PER_NODE = 60 * 12 + 11 * 2 + 2 * 8 + 4
-# DRAM bytes per local node of k_ax_df<8> from the ncu capture on the 24^3 mesh
-# (453.2 MB read + 49.5 MB written for 7,077,888 nodes), scaled to the 32^3 mesh
-DF_TRAFFIC_PER_NODE = (453.170944e6 + 49.525248e6) / 7077888
+# FP32-pipe operations per node of the folded FP64-accurate operator at N=7:
+# six folded contractions of 70 ops per output (4 compensated multiply-adds of
+# 12, a fold and a merge of 10, a normalisation of 2), the geometric step
+# (10 multiply-adds, 4 normalisations) and the final sums and weights
+# (profiles/sem_ax_dfeo_24cubed_N7.md measures 619 FMA-pipe ops per node)
+DF_OPS_PER_NODE = 6 * 70 + (10 * 12 + 4 * 2) + (2 * 8 + 2 * 12 + 3 * 2) + 4
+DF_KERNEL = "k_ax_dfeo<8>"
+# DRAM bytes per local node of k_ax_dfeo<8> from the ncu capture on the 24^3 mesh
+# (453.2 MB read + 47.0 MB written for 7,077,888 nodes), scaled to the 32^3 mesh
+DF_TRAFFIC_PER_NODE = (453.169408e6 + 46.974720e6) / 7077888
 FP64_PROBE_TFLOPS = 1.26  # FP64 FMA rate measured on this GPU model (probe: 2.2 FMA/clk/SM)
 
 
@@ -316,7 +319,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": df_ops, "peak": fp32_peak, "unit": "Tops/s",
                      "frac": df_ops / fp32_peak, "traffic": DF_TRAFFIC_PER_NODE * nL,
                      "peak_src": "128 FP32-pipe ops/clk/SM x SMs x max SM clock",
-                     "kernel": "k_ax_df<8>", "ops_per_node": DF_OPS_PER_NODE,
+                     "kernel": DF_KERNEL, "ops_per_node": DF_OPS_PER_NODE,
                      "hbm_achieved_gbs": hbm(BYTES_F64, avg64),
                      "hbm_frac": hbm(BYTES_F64, avg64) / pk["hbm_gbs"],
                      "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_src": pk["src"]},
