@@ -41,9 +41,9 @@ __global__ void __launch_bounds__(AxEoCfg<NP>::THREADS, 2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     dfp *sm = reinterpret_cast<dfp *>(smem_raw);
     dfp *stab = sm;
-    int *sexp = reinterpret_cast<int *>(sm + 4 * HH + (size_t)C::NE * 5 * C::NP3);
+    int *sexp = reinterpret_cast<int *>(sm + 4 * HH + (size_t)C::NE * 5 * C::SLAB);
     const int grp = threadIdx.x / C::NP2, tid = threadIdx.x - grp * C::NP2;
-    dfp *slab = sm + 4 * HH + (size_t)grp * 5 * C::NP3;
+    dfp *slab = sm + 4 * HH + (size_t)grp * 5 * C::SLAB;
     for (int t = threadIdx.x; t < 4 * HH; t += blockDim.x) stab[t] = tabs[t];
     for (int64_t e0 = (int64_t)blockIdx.x * C::NE; e0 < E; e0 += (int64_t)gridDim.x * C::NE) {
         const int64_t e = e0 + grp;

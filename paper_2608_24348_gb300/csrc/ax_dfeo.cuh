@@ -14,7 +14,8 @@
 // registers).  For r and s it folds one line of each direction into shared
 // memory, then computes the output pairs of H lines; results return to the
 // column owner through shared memory.  Shared memory per element: five
-// float-pair slabs of NP^3 values.
+// float-pair slabs of NP^2 lines, each line padded to NP+1 entries so that 32
+// threads reading 32 different lines at the same offset hit distinct banks.
 #pragma once
 
 #include "ax_df.cuh"
@@ -26,13 +27,15 @@ struct AxEoCfg {
     static constexpr int NE = (256 / NP2) > 0 ? (256 / NP2) : 1;
     static constexpr int THREADS = NE * NP2;
     static constexpr bool OK = (NP % 2) == 0;
+    static constexpr int LS = NP + 1;           // padded line stride of a slab
+    static constexpr int SLAB = NP2 * LS;       // float pairs per slab
 };
 
 // Half tables: A, B of D (gradient) and AT, BT of D^T (transpose), H*H each.
 template <int NP>
 __host__ __device__ constexpr size_t ax_dfeo_smem_bytes()
 {
-    return sizeof(dfp) * (4 * (NP / 2) * (NP / 2) + (size_t)AxEoCfg<NP>::NE * 5 * NP * NP * NP) +
+    return sizeof(dfp) * (4 * (NP / 2) * (NP / 2) + (size_t)AxEoCfg<NP>::NE * 5 * NP * NP * (NP + 1)) +
            sizeof(int) * AxEoCfg<NP>::NE;
 }
 
@@ -54,8 +57,9 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
                                                 int *sexp, int tid, bool active)
 {
     constexpr int H = NP / 2, NP2 = NP * NP, NP3 = NP2 * NP, HH = H * H;
+    constexpr int LS = AxEoCfg<NP>::LS, SL = AxEoCfg<NP>::SLAB;
     const dfp *tA = tab, *tB = tab + HH, *tAT = tab + 2 * HH, *tBT = tab + 3 * HH;
-    dfp *su = slab, *f1 = slab + NP3, *f2 = f1 + NP3, *g1 = f2 + NP3, *g2 = g1 + NP3;
+    dfp *su = slab, *f1 = slab + SL, *f2 = f1 + SL, *g1 = f2 + SL, *g2 = g1 + SL;
     const int i = tid % NP, j = tid / NP;
     // ---- load, element exponent, split
     double xu[NP];
@@ -77,14 +81,14 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
             ru[k] = df_split_scaled(xu[k], E);
-            su[k * NP2 + tid] = ru[k];
+            su[(k * NP + j) * LS + i] = ru[k];
         }
     }
     __syncthreads();
     // ---- fold the r-line (k = j, row i) into f1 and the s-line (k = j, column i) into f2
     if (active) {
-        const dfp *lr = su + (j * NP + i) * NP;
-        dfp *fr = f1 + (j * NP + i) * NP;
+        const dfp *lr = su + (j * NP + i) * LS;
+        dfp *fr = f1 + (j * NP + i) * LS;
 #pragma unroll
         for (int l = 0; l < H; ++l) {
             const dfp a = lr[l], b = lr[NP - 1 - l];
@@ -93,9 +97,9 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
         }
 #pragma unroll
         for (int l = 0; l < H; ++l) {
-            const dfp a = su[(j * NP + l) * NP + i], b = su[(j * NP + NP - 1 - l) * NP + i];
-            f2[(j * NP + l) * NP + i] = df_sum2(a, b);
-            f2[(j * NP + H + l) * NP + i] = df_sum2(a, df_neg(b));
+            const dfp a = su[(j * NP + l) * LS + i], b = su[(j * NP + NP - 1 - l) * LS + i];
+            f2[(j * NP + l) * LS + i] = df_sum2(a, b);
+            f2[(j * NP + H + l) * LS + i] = df_sum2(a, df_neg(b));
         }
     }
     __syncthreads();
@@ -106,7 +110,7 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
 #pragma unroll
         for (int kk = 0; kk < H; ++kk) {
             const int k = kr + kk;
-            const dfp *fr = f1 + (k * NP + j) * NP;
+            const dfp *fr = f1 + (k * NP + j) * LS;
             dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
 #pragma unroll
             for (int l = 0; l < H; ++l) {
@@ -114,8 +118,8 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
                 df_mad(b, tB[ip * H + l], fr[H + l]);
             }
             const dfp av = df_fin(a), bv = df_fin(b);
-            g1[(k * NP + j) * NP + ip] = df_sum2(av, bv);
-            g1[(k * NP + j) * NP + NP - 1 - ip] = df_sum2(bv, df_neg(av));
+            g1[(k * NP + j) * LS + ip] = df_sum2(av, bv);
+            g1[(k * NP + j) * LS + NP - 1 - ip] = df_sum2(bv, df_neg(av));
         }
         const int jp = j % H, ks = (j / H) * H;
 #pragma unroll
@@ -124,12 +128,12 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
             dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
 #pragma unroll
             for (int l = 0; l < H; ++l) {
-                df_mad(a, tA[jp * H + l], f2[(k * NP + l) * NP + i]);
-                df_mad(b, tB[jp * H + l], f2[(k * NP + H + l) * NP + i]);
+                df_mad(a, tA[jp * H + l], f2[(k * NP + l) * LS + i]);
+                df_mad(b, tB[jp * H + l], f2[(k * NP + H + l) * LS + i]);
             }
             const dfp av = df_fin(a), bv = df_fin(b);
-            g2[(k * NP + jp) * NP + i] = df_sum2(av, bv);
-            g2[(k * NP + NP - 1 - jp) * NP + i] = df_sum2(bv, df_neg(av));
+            g2[(k * NP + jp) * LS + i] = df_sum2(av, bv);
+            g2[(k * NP + NP - 1 - jp) * LS + i] = df_sum2(bv, df_neg(av));
         }
         dfp e[H], o[H];
 #pragma unroll
@@ -156,8 +160,8 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
     if (active) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            const int p = k * NP2 + tid;
-            const dfp ur = g1[p], us = g2[p];
+            const int p = k * NP2 + tid, q = (k * NP + j) * LS + i;
+            const dfp ur = g1[q], us = g2[q];
             const dfp g11 = geo[0 * NP3 + p], g22 = geo[1 * NP3 + p], g33 = geo[2 * NP3 + p];
             const dfp g12 = geo[3 * NP3 + p], g13 = geo[4 * NP3 + p], g23 = geo[5 * NP3 + p];
             const dfp bm = geo[6 * NP3 + p];
@@ -166,8 +170,8 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
             df_mad(vs, g12, ur); df_mad(vs, g22, us); df_mad(vs, g23, ut[k]);
             df_mad(vt, g13, ur); df_mad(vt, g23, us); df_mad(vt, g33, ut[k]);
             df_mad(vw, bm, ru[k]);
-            f1[p] = df_fin(vr);
-            f2[p] = df_fin(vs);
+            f1[q] = df_fin(vr);
+            f2[q] = df_fin(vs);
             ut[k] = df_fin(vt);  // ut now holds vt of this column
             rw[k] = df_fin(vw);
         }
@@ -175,8 +179,8 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
     __syncthreads();
     // ---- fold vr (r-line k = j, row i) into g1, vs (s-line k = j, column i) into g2
     if (active) {
-        const dfp *lr = f1 + (j * NP + i) * NP;
-        dfp *fr = g1 + (j * NP + i) * NP;
+        const dfp *lr = f1 + (j * NP + i) * LS;
+        dfp *fr = g1 + (j * NP + i) * LS;
 #pragma unroll
         for (int l = 0; l < H; ++l) {
             const dfp a = lr[l], b = lr[NP - 1 - l];
@@ -185,9 +189,9 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
         }
 #pragma unroll
         for (int l = 0; l < H; ++l) {
-            const dfp a = f2[(j * NP + l) * NP + i], b = f2[(j * NP + NP - 1 - l) * NP + i];
-            g2[(j * NP + l) * NP + i] = df_sum2(a, b);
-            g2[(j * NP + H + l) * NP + i] = df_sum2(a, df_neg(b));
+            const dfp a = f2[(j * NP + l) * LS + i], b = f2[(j * NP + NP - 1 - l) * LS + i];
+            g2[(j * NP + l) * LS + i] = df_sum2(a, b);
+            g2[(j * NP + H + l) * LS + i] = df_sum2(a, df_neg(b));
         }
     }
     __syncthreads();
@@ -198,7 +202,7 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
 #pragma unroll
         for (int kk = 0; kk < H; ++kk) {
             const int k = kr + kk;
-            const dfp *fr = g1 + (k * NP + j) * NP;
+            const dfp *fr = g1 + (k * NP + j) * LS;
             dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
 #pragma unroll
             for (int l = 0; l < H; ++l) {
@@ -206,8 +210,8 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
                 df_mad(b, tBT[ip * H + l], fr[H + l]);
             }
             const dfp av = df_fin(a), bv = df_fin(b);
-            f1[(k * NP + j) * NP + ip] = df_sum2(av, bv);
-            f1[(k * NP + j) * NP + NP - 1 - ip] = df_sum2(bv, df_neg(av));
+            f1[(k * NP + j) * LS + ip] = df_sum2(av, bv);
+            f1[(k * NP + j) * LS + NP - 1 - ip] = df_sum2(bv, df_neg(av));
         }
         const int jp = j % H, ks = (j / H) * H;
 #pragma unroll
@@ -216,12 +220,12 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
             dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
 #pragma unroll
             for (int l = 0; l < H; ++l) {
-                df_mad(a, tAT[jp * H + l], g2[(k * NP + l) * NP + i]);
-                df_mad(b, tBT[jp * H + l], g2[(k * NP + H + l) * NP + i]);
+                df_mad(a, tAT[jp * H + l], g2[(k * NP + l) * LS + i]);
+                df_mad(b, tBT[jp * H + l], g2[(k * NP + H + l) * LS + i]);
             }
             const dfp av = df_fin(a), bv = df_fin(b);
-            f2[(k * NP + jp) * NP + i] = df_sum2(av, bv);
-            f2[(k * NP + NP - 1 - jp) * NP + i] = df_sum2(bv, df_neg(av));
+            f2[(k * NP + jp) * LS + i] = df_sum2(av, bv);
+            f2[(k * NP + NP - 1 - jp) * LS + i] = df_sum2(bv, df_neg(av));
         }
         dfp e[H], o[H];
 #pragma unroll
@@ -247,10 +251,10 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
     if (active) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            const int p = k * NP2 + tid;
+            const int p = k * NP2 + tid, q = (k * NP + j) * LS + i;
             dfacc s = {wt[k].hi, wt[k].lo};
-            df_add(s, f1[p]);
-            df_add(s, f2[p]);
+            df_add(s, f1[q]);
+            df_add(s, f2[q]);
             dfacc o = {0.f, 0.f};
             df_mad(o, h1, df_fin(s));
             df_mad(o, h2, rw[k]);
