@@ -80,6 +80,18 @@ __device__ __forceinline__ double df_join_scaled(dfp a, int E)
     return __longlong_as_double(b + ((long long)E << 52));
 }
 
+// A = a * b: a fresh accumulator holding one exact product (TwoProd) plus the
+// cross terms; the same value df_mad would give from a zero accumulator, eight
+// operations cheaper.
+__device__ __forceinline__ dfacc df_mul(dfp a, dfp b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float err = __fmaf_rn(a.hi, b.hi, -p);
+    err = __fmaf_rn(a.hi, b.lo, err);
+    err = __fmaf_rn(a.lo, b.hi, err);
+    return {p, err};
+}
+
 // A += a * b   (a, b float pairs)
 __device__ __forceinline__ void df_mad(dfacc &A, dfp a, dfp b)
 {
@@ -103,6 +115,21 @@ __device__ __forceinline__ void df_add(dfacc &A, dfp a)
     A.s = s;
     A.e = __fadd_rn(A.e, __fadd_rn(t, a.lo));
 }
+
+// a + b as a pair that is not renormalised: TwoSum of the leading parts, both
+// trailing parts added to the error term (8 operations).  Every consumer of a
+// pair (df_mad, df_add, TwoSum, the final FP64 join) is exact or error-bounded
+// for such pairs, so renormalising between stages buys no accuracy.
+__device__ __forceinline__ dfp df_sum(dfp a, dfp b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bv = __fsub_rn(s, a.hi);
+    const float t = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));
+    return {s, __fadd_rn(t, __fadd_rn(a.lo, b.lo))};
+}
+
+// The accumulator as a pair, without renormalising.
+__device__ __forceinline__ dfp df_raw(dfacc A) { return {A.s, A.e}; }
 
 // Normalised pair of the accumulator (FastTwoSum).
 __device__ __forceinline__ dfp df_fin(dfacc A)
@@ -175,46 +202,49 @@ __device__ __forceinline__ void ax_df_element(const Load &load, const Store &sto
     if (active) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            dfacc ar = {0.f, 0.f}, as = {0.f, 0.f}, at = {0.f, 0.f};
+            dfacc ar = df_mul(sDT[i], su[k * NP2 + j * NP]);
+            dfacc as = df_mul(sDT[j], su[k * NP2 + i]);
+            dfacc at = df_mul(sDT[k], ru[0]);
 #pragma unroll
-            for (int l = 0; l < NP; ++l) {
+            for (int l = 1; l < NP; ++l) {
                 df_mad(ar, sDT[l * NP + i], su[k * NP2 + j * NP + l]);
                 df_mad(as, sDT[l * NP + j], su[k * NP2 + l * NP + i]);
                 df_mad(at, sDT[l * NP + k], ru[l]);
             }
-            const dfp ur = df_fin(ar), us = df_fin(as), ut = df_fin(at);
+            const dfp ur = df_raw(ar), us = df_raw(as), ut = df_raw(at);
             const int p = k * NP2 + tid;
             const dfp g11 = geo[0 * NP3 + p], g22 = geo[1 * NP3 + p], g33 = geo[2 * NP3 + p];
             const dfp g12 = geo[3 * NP3 + p], g13 = geo[4 * NP3 + p], g23 = geo[5 * NP3 + p];
             const dfp bm = geo[6 * NP3 + p];
-            dfacc vr = {0.f, 0.f}, vs = {0.f, 0.f}, vt = {0.f, 0.f}, vw = {0.f, 0.f};
-            df_mad(vr, g11, ur); df_mad(vr, g12, us); df_mad(vr, g13, ut);
-            df_mad(vs, g12, ur); df_mad(vs, g22, us); df_mad(vs, g23, ut);
-            df_mad(vt, g13, ur); df_mad(vt, g23, us); df_mad(vt, g33, ut);
-            df_mad(vw, bm, ru[k]);
-            svr[p] = df_fin(vr);
-            svs[p] = df_fin(vs);
-            rvt[k] = df_fin(vt);
-            rw[k] = df_fin(vw);
+            dfacc vr = df_mul(g11, ur), vs = df_mul(g12, ur), vt = df_mul(g13, ur);
+            df_mad(vr, g12, us); df_mad(vr, g13, ut);
+            df_mad(vs, g22, us); df_mad(vs, g23, ut);
+            df_mad(vt, g23, us); df_mad(vt, g33, ut);
+            const dfacc vw = df_mul(bm, ru[k]);
+            svr[p] = df_raw(vr);
+            svs[p] = df_raw(vs);
+            rvt[k] = df_raw(vt);
+            rw[k] = df_raw(vw);
         }
     }
     __syncthreads();
     if (active) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            dfacc ar = {0.f, 0.f}, as = {0.f, 0.f}, at = {0.f, 0.f};  // three independent chains
+            dfacc ar = df_mul(sD[i], svr[k * NP2 + j * NP]);  // three independent chains
+            dfacc as = df_mul(sD[j], svs[k * NP2 + i]);
+            dfacc at = df_mul(sD[k], rvt[0]);
 #pragma unroll
-            for (int l = 0; l < NP; ++l) {
+            for (int l = 1; l < NP; ++l) {
                 df_mad(ar, sD[l * NP + i], svr[k * NP2 + j * NP + l]);
                 df_mad(as, sD[l * NP + j], svs[k * NP2 + l * NP + i]);
                 df_mad(at, sD[l * NP + k], rvt[l]);
             }
-            df_add(ar, df_fin(as));
-            df_add(ar, df_fin(at));
-            dfacc o = {0.f, 0.f};
-            df_mad(o, h1, df_fin(ar));
+            df_add(ar, df_raw(as));
+            df_add(ar, df_raw(at));
+            dfacc o = df_mul(h1, df_raw(ar));
             df_mad(o, h2, rw[k]);
-            store(k * NP2 + tid, df_join_scaled(df_fin(o), E));
+            store(k * NP2 + tid, df_join_scaled(df_raw(o), E));
         }
     }
     __syncthreads();
@@ -254,39 +284,42 @@ __device__ __forceinline__ void ax_df_element_lowreg(const Load &load, const Sto
     __syncthreads();
     for (int q = threadIdx.x; q < NP3; q += blockDim.x) {
         const int i = q % NP, j = (q / NP) % NP, k = q / NP2;
-        dfacc ar = {0.f, 0.f}, as = {0.f, 0.f}, at = {0.f, 0.f};
-        for (int l = 0; l < NP; ++l) {
+        dfacc ar = df_mul(sDT[i], su[(k * NP + j) * NP]);
+        dfacc as = df_mul(sDT[j], su[k * NP2 + i]);
+        dfacc at = df_mul(sDT[k], su[j * NP + i]);
+        for (int l = 1; l < NP; ++l) {
             df_mad(ar, sDT[l * NP + i], su[(k * NP + j) * NP + l]);
             df_mad(as, sDT[l * NP + j], su[(k * NP + l) * NP + i]);
             df_mad(at, sDT[l * NP + k], su[(l * NP + j) * NP + i]);
         }
-        const dfp ur = df_fin(ar), us = df_fin(as), ut = df_fin(at);
+        const dfp ur = df_raw(ar), us = df_raw(as), ut = df_raw(at);
         const dfp g11 = geo[0 * NP3 + q], g22 = geo[1 * NP3 + q], g33 = geo[2 * NP3 + q];
         const dfp g12 = geo[3 * NP3 + q], g13 = geo[4 * NP3 + q], g23 = geo[5 * NP3 + q];
-        dfacc vr = {0.f, 0.f}, vs = {0.f, 0.f}, vt = {0.f, 0.f};
-        df_mad(vr, g11, ur); df_mad(vr, g12, us); df_mad(vr, g13, ut);
-        df_mad(vs, g12, ur); df_mad(vs, g22, us); df_mad(vs, g23, ut);
-        df_mad(vt, g13, ur); df_mad(vt, g23, us); df_mad(vt, g33, ut);
-        svr[q] = df_fin(vr);
-        svs[q] = df_fin(vs);
-        svt[q] = df_fin(vt);
+        dfacc vr = df_mul(g11, ur), vs = df_mul(g12, ur), vt = df_mul(g13, ur);
+        df_mad(vr, g12, us); df_mad(vr, g13, ut);
+        df_mad(vs, g22, us); df_mad(vs, g23, ut);
+        df_mad(vt, g23, us); df_mad(vt, g33, ut);
+        svr[q] = df_raw(vr);
+        svs[q] = df_raw(vs);
+        svt[q] = df_raw(vt);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < NP3; q += blockDim.x) {
         const int i = q % NP, j = (q / NP) % NP, k = q / NP2;
-        dfacc ar = {0.f, 0.f}, as = {0.f, 0.f}, at = {0.f, 0.f};
-        for (int l = 0; l < NP; ++l) {
+        dfacc ar = df_mul(sD[i], svr[(k * NP + j) * NP]);
+        dfacc as = df_mul(sD[j], svs[k * NP2 + i]);
+        dfacc at = df_mul(sD[k], svt[j * NP + i]);
+        for (int l = 1; l < NP; ++l) {
             df_mad(ar, sD[l * NP + i], svr[(k * NP + j) * NP + l]);
             df_mad(as, sD[l * NP + j], svs[(k * NP + l) * NP + i]);
             df_mad(at, sD[l * NP + k], svt[(l * NP + j) * NP + i]);
         }
-        df_add(ar, df_fin(as));
-        df_add(ar, df_fin(at));
-        dfacc o = {0.f, 0.f}, bu = {0.f, 0.f};
-        df_mad(bu, geo[6 * NP3 + q], su[q]);
-        df_mad(o, h1, df_fin(ar));
-        df_mad(o, h2, df_fin(bu));
-        store(q, df_join_scaled(df_fin(o), E));
+        df_add(ar, df_raw(as));
+        df_add(ar, df_raw(at));
+        const dfacc bu = df_mul(geo[6 * NP3 + q], su[q]);
+        dfacc o = df_mul(h1, df_raw(ar));
+        df_mad(o, h2, df_raw(bu));
+        store(q, df_join_scaled(df_raw(o), E));
     }
     __syncthreads();
 }

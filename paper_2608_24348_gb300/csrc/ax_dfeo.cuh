@@ -8,7 +8,8 @@
 //     a_i = sum_l A_il e_l,  b_i = sum_l B_il o_l,
 //     (Du)_i = a_i + b_i,    (Du)_{NP-1-i} = b_i - a_i          (i < H),
 // which halves the multiply-adds of all six directional contractions.  The
-// arithmetic is the float-pair compensated arithmetic of ax_df.cuh.
+// arithmetic is the float-pair compensated arithmetic of ax_df.cuh; pairs pass
+// between stages without renormalisation.
 //
 // Thread (i, j) of an element owns column u[.][j][i] (the t direction stays in
 // registers).  For r and s it folds one line of each direction into shared
@@ -37,14 +38,6 @@ __host__ __device__ constexpr size_t ax_dfeo_smem_bytes()
 {
     return sizeof(dfp) * (4 * (NP / 2) * (NP / 2) + (size_t)AxEoCfg<NP>::NE * 5 * NP * NP * (NP + 1)) +
            sizeof(int) * AxEoCfg<NP>::NE;
-}
-
-// Fold a line: e[l] = x[l] + x[NP-1-l], o[l] = x[l] - x[NP-1-l] (float pairs).
-__device__ __forceinline__ dfp df_sum2(dfp a, dfp b)
-{
-    dfacc A = {a.hi, a.lo};
-    df_add(A, b);
-    return df_fin(A);
 }
 
 __device__ __forceinline__ dfp df_neg(dfp a) { return {-a.hi, -a.lo}; }
@@ -92,14 +85,14 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
 #pragma unroll
         for (int l = 0; l < H; ++l) {
             const dfp a = lr[l], b = lr[NP - 1 - l];
-            fr[l] = df_sum2(a, b);
-            fr[H + l] = df_sum2(a, df_neg(b));
+            fr[l] = df_sum(a, b);
+            fr[H + l] = df_sum(a, df_neg(b));
         }
 #pragma unroll
         for (int l = 0; l < H; ++l) {
             const dfp a = su[(j * NP + l) * LS + i], b = su[(j * NP + NP - 1 - l) * LS + i];
-            f2[(j * NP + l) * LS + i] = df_sum2(a, b);
-            f2[(j * NP + H + l) * LS + i] = df_sum2(a, df_neg(b));
+            f2[(j * NP + l) * LS + i] = df_sum(a, b);
+            f2[(j * NP + H + l) * LS + i] = df_sum(a, df_neg(b));
         }
     }
     __syncthreads();
@@ -111,47 +104,48 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
         for (int kk = 0; kk < H; ++kk) {
             const int k = kr + kk;
             const dfp *fr = f1 + (k * NP + j) * LS;
-            dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
+            dfacc a = df_mul(tA[ip * H], fr[0]), b = df_mul(tB[ip * H], fr[H]);
 #pragma unroll
-            for (int l = 0; l < H; ++l) {
+            for (int l = 1; l < H; ++l) {
                 df_mad(a, tA[ip * H + l], fr[l]);
                 df_mad(b, tB[ip * H + l], fr[H + l]);
             }
-            const dfp av = df_fin(a), bv = df_fin(b);
-            g1[(k * NP + j) * LS + ip] = df_sum2(av, bv);
-            g1[(k * NP + j) * LS + NP - 1 - ip] = df_sum2(bv, df_neg(av));
+            const dfp av = df_raw(a), bv = df_raw(b);
+            g1[(k * NP + j) * LS + ip] = df_sum(av, bv);
+            g1[(k * NP + j) * LS + NP - 1 - ip] = df_sum(bv, df_neg(av));
         }
         const int jp = j % H, ks = (j / H) * H;
 #pragma unroll
         for (int kk = 0; kk < H; ++kk) {
             const int k = ks + kk;
-            dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
+            dfacc a = df_mul(tA[jp * H], f2[(k * NP) * LS + i]);
+            dfacc b = df_mul(tB[jp * H], f2[(k * NP + H) * LS + i]);
 #pragma unroll
-            for (int l = 0; l < H; ++l) {
+            for (int l = 1; l < H; ++l) {
                 df_mad(a, tA[jp * H + l], f2[(k * NP + l) * LS + i]);
                 df_mad(b, tB[jp * H + l], f2[(k * NP + H + l) * LS + i]);
             }
-            const dfp av = df_fin(a), bv = df_fin(b);
-            g2[(k * NP + jp) * LS + i] = df_sum2(av, bv);
-            g2[(k * NP + NP - 1 - jp) * LS + i] = df_sum2(bv, df_neg(av));
+            const dfp av = df_raw(a), bv = df_raw(b);
+            g2[(k * NP + jp) * LS + i] = df_sum(av, bv);
+            g2[(k * NP + NP - 1 - jp) * LS + i] = df_sum(bv, df_neg(av));
         }
         dfp e[H], o[H];
 #pragma unroll
         for (int l = 0; l < H; ++l) {
-            e[l] = df_sum2(ru[l], ru[NP - 1 - l]);
-            o[l] = df_sum2(ru[l], df_neg(ru[NP - 1 - l]));
+            e[l] = df_sum(ru[l], ru[NP - 1 - l]);
+            o[l] = df_sum(ru[l], df_neg(ru[NP - 1 - l]));
         }
 #pragma unroll
         for (int kp = 0; kp < H; ++kp) {
-            dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
+            dfacc a = df_mul(tA[kp * H], e[0]), b = df_mul(tB[kp * H], o[0]);
 #pragma unroll
-            for (int l = 0; l < H; ++l) {
+            for (int l = 1; l < H; ++l) {
                 df_mad(a, tA[kp * H + l], e[l]);
                 df_mad(b, tB[kp * H + l], o[l]);
             }
-            const dfp av = df_fin(a), bv = df_fin(b);
-            ut[kp] = df_sum2(av, bv);
-            ut[NP - 1 - kp] = df_sum2(bv, df_neg(av));
+            const dfp av = df_raw(a), bv = df_raw(b);
+            ut[kp] = df_sum(av, bv);
+            ut[NP - 1 - kp] = df_sum(bv, df_neg(av));
         }
     }
     __syncthreads();
@@ -165,15 +159,15 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
             const dfp g11 = geo[0 * NP3 + p], g22 = geo[1 * NP3 + p], g33 = geo[2 * NP3 + p];
             const dfp g12 = geo[3 * NP3 + p], g13 = geo[4 * NP3 + p], g23 = geo[5 * NP3 + p];
             const dfp bm = geo[6 * NP3 + p];
-            dfacc vr = {0.f, 0.f}, vs = {0.f, 0.f}, vt = {0.f, 0.f}, vw = {0.f, 0.f};
-            df_mad(vr, g11, ur); df_mad(vr, g12, us); df_mad(vr, g13, ut[k]);
-            df_mad(vs, g12, ur); df_mad(vs, g22, us); df_mad(vs, g23, ut[k]);
-            df_mad(vt, g13, ur); df_mad(vt, g23, us); df_mad(vt, g33, ut[k]);
-            df_mad(vw, bm, ru[k]);
-            f1[q] = df_fin(vr);
-            f2[q] = df_fin(vs);
-            ut[k] = df_fin(vt);  // ut now holds vt of this column
-            rw[k] = df_fin(vw);
+            dfacc vr = df_mul(g11, ur), vs = df_mul(g12, ur), vt = df_mul(g13, ur);
+            df_mad(vr, g12, us); df_mad(vr, g13, ut[k]);
+            df_mad(vs, g22, us); df_mad(vs, g23, ut[k]);
+            df_mad(vt, g23, us); df_mad(vt, g33, ut[k]);
+            const dfacc vw = df_mul(bm, ru[k]);
+            f1[q] = df_raw(vr);
+            f2[q] = df_raw(vs);
+            ut[k] = df_raw(vt);  // ut now holds vt of this column
+            rw[k] = df_raw(vw);
         }
     }
     __syncthreads();
@@ -184,14 +178,14 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
 #pragma unroll
         for (int l = 0; l < H; ++l) {
             const dfp a = lr[l], b = lr[NP - 1 - l];
-            fr[l] = df_sum2(a, b);
-            fr[H + l] = df_sum2(a, df_neg(b));
+            fr[l] = df_sum(a, b);
+            fr[H + l] = df_sum(a, df_neg(b));
         }
 #pragma unroll
         for (int l = 0; l < H; ++l) {
             const dfp a = f2[(j * NP + l) * LS + i], b = f2[(j * NP + NP - 1 - l) * LS + i];
-            g2[(j * NP + l) * LS + i] = df_sum2(a, b);
-            g2[(j * NP + H + l) * LS + i] = df_sum2(a, df_neg(b));
+            g2[(j * NP + l) * LS + i] = df_sum(a, b);
+            g2[(j * NP + H + l) * LS + i] = df_sum(a, df_neg(b));
         }
     }
     __syncthreads();
@@ -203,47 +197,48 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
         for (int kk = 0; kk < H; ++kk) {
             const int k = kr + kk;
             const dfp *fr = g1 + (k * NP + j) * LS;
-            dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
+            dfacc a = df_mul(tAT[ip * H], fr[0]), b = df_mul(tBT[ip * H], fr[H]);
 #pragma unroll
-            for (int l = 0; l < H; ++l) {
+            for (int l = 1; l < H; ++l) {
                 df_mad(a, tAT[ip * H + l], fr[l]);
                 df_mad(b, tBT[ip * H + l], fr[H + l]);
             }
-            const dfp av = df_fin(a), bv = df_fin(b);
-            f1[(k * NP + j) * LS + ip] = df_sum2(av, bv);
-            f1[(k * NP + j) * LS + NP - 1 - ip] = df_sum2(bv, df_neg(av));
+            const dfp av = df_raw(a), bv = df_raw(b);
+            f1[(k * NP + j) * LS + ip] = df_sum(av, bv);
+            f1[(k * NP + j) * LS + NP - 1 - ip] = df_sum(bv, df_neg(av));
         }
         const int jp = j % H, ks = (j / H) * H;
 #pragma unroll
         for (int kk = 0; kk < H; ++kk) {
             const int k = ks + kk;
-            dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
+            dfacc a = df_mul(tAT[jp * H], g2[(k * NP) * LS + i]);
+            dfacc b = df_mul(tBT[jp * H], g2[(k * NP + H) * LS + i]);
 #pragma unroll
-            for (int l = 0; l < H; ++l) {
+            for (int l = 1; l < H; ++l) {
                 df_mad(a, tAT[jp * H + l], g2[(k * NP + l) * LS + i]);
                 df_mad(b, tBT[jp * H + l], g2[(k * NP + H + l) * LS + i]);
             }
-            const dfp av = df_fin(a), bv = df_fin(b);
-            f2[(k * NP + jp) * LS + i] = df_sum2(av, bv);
-            f2[(k * NP + NP - 1 - jp) * LS + i] = df_sum2(bv, df_neg(av));
+            const dfp av = df_raw(a), bv = df_raw(b);
+            f2[(k * NP + jp) * LS + i] = df_sum(av, bv);
+            f2[(k * NP + NP - 1 - jp) * LS + i] = df_sum(bv, df_neg(av));
         }
         dfp e[H], o[H];
 #pragma unroll
         for (int l = 0; l < H; ++l) {
-            e[l] = df_sum2(ut[l], ut[NP - 1 - l]);
-            o[l] = df_sum2(ut[l], df_neg(ut[NP - 1 - l]));
+            e[l] = df_sum(ut[l], ut[NP - 1 - l]);
+            o[l] = df_sum(ut[l], df_neg(ut[NP - 1 - l]));
         }
 #pragma unroll
         for (int kp = 0; kp < H; ++kp) {
-            dfacc a = {0.f, 0.f}, b = {0.f, 0.f};
+            dfacc a = df_mul(tAT[kp * H], e[0]), b = df_mul(tBT[kp * H], o[0]);
 #pragma unroll
-            for (int l = 0; l < H; ++l) {
+            for (int l = 1; l < H; ++l) {
                 df_mad(a, tAT[kp * H + l], e[l]);
                 df_mad(b, tBT[kp * H + l], o[l]);
             }
-            const dfp av = df_fin(a), bv = df_fin(b);
-            wt[kp] = df_sum2(av, bv);
-            wt[NP - 1 - kp] = df_sum2(bv, df_neg(av));
+            const dfp av = df_raw(a), bv = df_raw(b);
+            wt[kp] = df_sum(av, bv);
+            wt[NP - 1 - kp] = df_sum(bv, df_neg(av));
         }
     }
     __syncthreads();
@@ -255,10 +250,9 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
             dfacc s = {wt[k].hi, wt[k].lo};
             df_add(s, f1[q]);
             df_add(s, f2[q]);
-            dfacc o = {0.f, 0.f};
-            df_mad(o, h1, df_fin(s));
+            dfacc o = df_mul(h1, df_raw(s));
             df_mad(o, h2, rw[k]);
-            store(p, df_join_scaled(df_fin(o), E));
+            store(p, df_join_scaled(df_raw(o), E));
         }
     }
     __syncthreads();

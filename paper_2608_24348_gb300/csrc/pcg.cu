@@ -76,6 +76,7 @@ static void fill_desc(const sem_ctx *c, const sem_ws &ws, const double *b, doubl
     d.D64 = c->tab64 + 2 * c->n;
     d.D32 = c->tab32 + 2 * c->n;
     d.Ddf = (const dfp *)c->tabdf;
+    d.Ddfeo = (const dfp *)c->tabdfeo;
     d.b = b;
     d.x = x;
     d.r = ws.r;

@@ -38,6 +38,7 @@
 
 #include "ax.cuh"
 #include "ax_df.cuh"
+#include "ax_dfeo.cuh"
 #include "ax_tc.cuh"
 #include "common.cuh"
 #include "gs.cuh"
@@ -50,6 +51,10 @@
 #endif
 #ifndef SEM_SOLVE_F32_MINB
 #define SEM_SOLVE_F32_MINB 3
+#endif
+// FP64-accurate element phases of even orders use the folded operator.
+#ifndef SEM_SOLVE_DF_FOLDED
+#define SEM_SOLVE_DF_FOLDED 1
 #endif
 
 // Which element operators a solver kernel carries (keeps each kernel's
@@ -74,6 +79,7 @@ struct ProbDesc {
     const double *D64;
     const float *D32;
     const dfp *Ddf;
+    const dfp *Ddfeo;   // folded half tables (even orders)
     const double *b;
     double *x;
     double *r, *p, *w, *minv;
@@ -300,6 +306,63 @@ __device__ __forceinline__ void elem_item_df(const ProbDesc &P, double alpha, do
     }
 }
 
+// The same phases with the folded (even-odd) float-pair operator, even orders.
+template <int NP>
+constexpr bool df_folded()
+{
+    // (and only while two blocks still fit on an SM)
+    return SEM_SOLVE_DF_FOLDED && AxEoCfg<NP>::OK && AxEoCfg<NP>::THREADS <= SEM_SOLVE_THREADS &&
+           ax_dfeo_smem_bytes<NP>() <= 112 * 1024;
+}
+
+template <int NP, int KIND>
+__device__ __forceinline__ void elem_item_dfeo(const ProbDesc &P, double alpha, double beta, int first,
+                                               int64_t g, unsigned char *smem, double &acc)
+{
+    using C = AxEoCfg<NP>;
+    constexpr int HH = (NP / 2) * (NP / 2);
+    dfp *sm = reinterpret_cast<dfp *>(smem);
+    dfp *stab = sm;
+    int *sexp = reinterpret_cast<int *>(sm + 4 * HH + (size_t)C::NE * 5 * C::SLAB);
+    const int grp = threadIdx.x / C::NP2;
+    const int tid = threadIdx.x - grp * C::NP2;
+    const bool inrange = grp < C::NE;
+    const int64_t e = g * C::NE + grp;
+    const bool active = inrange && e < P.E;
+    dfp *slab = sm + 4 * HH + (size_t)(inrange ? grp : 0) * 5 * C::SLAB;
+    const int64_t off = (active ? e : 0) * C::NP3;
+    const dfp *geo = P.geodf + (active ? e : 0) * 7 * C::NP3;
+    const float h1h = (float)P.h1, h2h = (float)P.h2;
+    const dfp H1 = {h1h, (float)(P.h1 - (double)h1h)}, H2 = {h2h, (float)(P.h2 - (double)h2h)};
+    for (int t = threadIdx.x; t < 4 * HH; t += blockDim.x) stab[t] = P.Ddfeo[t];
+    int *myexp = sexp + (inrange ? grp : 0);
+    if (KIND == 0) {
+        const double *x = P.x + off;
+        double *w = P.w + off;
+        auto load = [&](int q) { return __ldcg(x + q); };
+        auto store = [&](int q, double v) { w[q] = v; };
+        ax_dfeo_element<NP>(load, store, geo, H1, H2, stab, slab, myexp, tid, active);
+    } else {
+        const double *r = P.r + off, *mi = P.minv + off;
+        double *p = P.p + off, *w = P.w + off, *x = P.x + off;
+        auto load = [&](int q) {
+            double pn = __ldcg(mi + q) * __ldcg(r + q);
+            if (!first) {
+                const double po = __ldcg(p + q);
+                x[q] = fma(alpha, po, __ldcg(x + q));
+                pn = fma(beta, po, pn);
+            }
+            p[q] = pn;
+            return pn;
+        };
+        auto store = [&](int q, double v) {
+            w[q] = v;
+            acc = fma(__ldcg(p + q), v, acc);
+        };
+        ax_dfeo_element<NP>(load, store, geo, H1, H2, stab, slab, myexp, tid, active);
+    }
+}
+
 // FP64-accurate w = A x with the low-register float-pair operator (mixed
 // modes: the FP64 residual of each refinement step); the NE elements of
 // group g one after another.
@@ -348,7 +411,12 @@ __device__ __forceinline__ void elem_dispatch_np(const ProbDesc &P, int ph, doub
                                                  int first, int64_t g, int tc, unsigned char *smem,
                                                  double &acc)
 {
-    if constexpr (MODE == MODE_F64) {
+    if constexpr (MODE == MODE_F64 && df_folded<NP>()) {
+        if (ph == PH_AX0)
+            elem_item_dfeo<NP, 0>(P, alpha, beta, first, g, smem, acc);
+        else
+            elem_item_dfeo<NP, 1>(P, alpha, beta, first, g, smem, acc);
+    } else if constexpr (MODE == MODE_F64) {
         if (ph == PH_AX0)
             elem_item_df<NP, 0>(P, alpha, beta, first, g, smem, acc);
         else
@@ -878,7 +946,7 @@ template <int NP, int MODE>
 constexpr size_t solve_smem_np()
 {
     return MODE == MODE_F64N ? ax_smem_bytes<NP, double>()
-           : MODE == MODE_F64 ? ax_df_smem_bytes<NP>()
+           : MODE == MODE_F64 ? (df_folded<NP>() ? ax_dfeo_smem_bytes<NP>() : ax_df_smem_bytes<NP>())
            : MODE == MODE_F32 ? sem_max_sz(ax_smem_bytes<NP, float>(), ax_df_lowreg_smem_bytes<NP>())
                               : sem_max_sz(ax_tc_smem_bytes<NP>(), ax_df_lowreg_smem_bytes<NP>());
 }

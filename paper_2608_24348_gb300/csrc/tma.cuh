@@ -76,3 +76,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     }
     return true;
 }
+
+// Hint: start moving [src, src + bytes) from HBM into L2 (bytes a multiple of
+// 16, src 16-byte aligned).  Nothing completes or waits; a later load of the
+// same lines finds them in L2.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// L2 prefetch of the bytes [begin, end) of a buffer, shrunk to whole 16-byte
+// units inside it, so no prefetched byte lies outside the buffer.
+__device__ __forceinline__ void l2_prefetch_span(const void *base, int64_t begin, int64_t end)
+{
+    const uintptr_t b = ((uintptr_t)base + (uintptr_t)begin + 15) & ~(uintptr_t)15;
+    const uintptr_t e = ((uintptr_t)base + (uintptr_t)end) & ~(uintptr_t)15;
+    if (e > b) bulk_prefetch_l2((const void *)b, (uint32_t)(e - b));
+}
