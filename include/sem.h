@@ -258,6 +258,38 @@ typedef struct {
 SEM_API int sem_tgv_init(sem_ctx *ctx, double nu, double dt, sem_dtype op, const sem_solve_opts *vel,
                  const sem_solve_opts *pres, sem_tgv **out);
 
+/* Three-level precision policy of the stepper (Sec. 2, Fig. 2; the configurations
+ * of Table 2).  One rule gives, per program block, the precision of each role:
+ *  - sem: compute precision of the dealiased convection (the SEM block):
+ *    SEM_F64, SEM_F32, or the kernel-level overrides SEM_F16_TC / SEM_BF16_TC =
+ *    every operand of its contractions rounded to FP16 / BF16, FP32 accumulation;
+ *  - vel, pres: compute precision of the three velocity Helmholtz solves and of
+ *    the pressure Poisson solve: SEM_F64 (PCG on the FP64-accurate operator),
+ *    SEM_F64_NATIVE, SEM_F32 (FP32 inner PCG inside FP64 refinement to the same
+ *    tolerance) or the kernel-level ax_helm overrides SEM_F16_TC / SEM_BF16_TC
+ *    (16-bit tensor-core operator in that inner PCG);
+ *  - storage: the global cap rp on stored state: SEM_F64, or SEM_F32 = the
+ *    velocity and convection histories and the pressure are rounded to FP32
+ *    values where they are stored each step (FP32 storage numerics; the buffers
+ *    stay FP64).
+ * Accumulation (dot products, norms, refinement residuals, BDF/EXT sums, the
+ * KE / enstrophy diagnostics) is FP64 under every rule.  first_step: the rule
+ * applies from that step on (1-based; <= 1 = from the first step). */
+typedef struct {
+    int first_step;
+    sem_dtype sem, vel, pres, storage;
+} sem_tgv_policy;
+
+#define SEM_TGV_MAX_RULES 8
+
+/* Replace the stepper's policy schedule by n <= SEM_TGV_MAX_RULES rules in
+ * non-decreasing first_step order.  At each step the last rule whose first_step
+ * <= that step is in force; before the first rule starts (and with n = 0) the
+ * precisions given to sem_tgv_init apply.  A change of rule between two steps
+ * re-captures the step graph.  Returns SEM_ERR_ARG for an unsupported
+ * precision or an unsorted schedule (the previous schedule then stays). */
+SEM_API int sem_tgv_set_policy(sem_tgv *tgv, int n, const sem_tgv_policy *rules);
+
 /* Set the state at history level (0 = u^n, 1 = u^{n-1}, 2 = u^{n-2}) from
  * FP64 E-vectors u, v, w (and p for level 0; may be NULL); step is the number
  * of steps already taken (selects the startup order), t the time. */

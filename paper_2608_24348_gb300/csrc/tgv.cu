@@ -11,6 +11,11 @@
 //   5. (nu A + b0/dt B) u_c = dssum( F_c + B (sum_j b_j u_c/dt - dp/dx_c) )
 //                                                   (k_tgv_vrhs + 3-problem batched PCG)
 //   6. shift histories; KE and enstrophy into a device log      (k_tgv_diag_*)
+// Precision policy (Sec. 2, Fig. 2): the rule in force at a step selects the
+// convection precision (FP64, FP32, or FP16/BF16 operands with FP32
+// accumulation), the inner precision of the velocity and pressure solves, and
+// whether the stored state (velocity and convection histories, pressure) is
+// rounded to FP32 values where it is stored.
 // Histories, right-hand sides and diagnostics are FP64.  With op = SEM_F32 the
 // convective term is computed in FP32; the solves use the precision of the
 // options passed (the default pressure options then select an FP32 inner PCG
@@ -20,6 +25,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "gs.cuh"
@@ -52,8 +60,12 @@ struct TgvDev {       // device-side counters
 struct sem_tgv {
     sem_ctx *c;
     double nu, dt;
-    sem_dtype op;
-    sem_solve_opts vo, po;
+    sem_dtype op;          // convection precision in force
+    sem_dtype storage;     // stored-state precision in force (SEM_F64 or SEM_F32)
+    sem_solve_opts vo, po; // solve options in force
+    sem_dtype op0, vin0, pin0;  // the precisions given to sem_tgv_init
+    sem_tgv_policy rules[SEM_TGV_MAX_RULES];
+    int nrules, cur_rule;  // cur_rule: -1 = init precisions, -2 = not applied yet
     int step, M;
     double t;
     double *u[3][3], *C[3][3], *p, *unew[3], *F[3], *g[3], *bp, *rhs[3];
@@ -160,8 +172,20 @@ struct ConvArgs {
     int64_t E;
 };
 
+// Operand rounding of the 16-bit convection overrides: R16 = 1 FP16, 2 BF16.
+template <int R16, typename T>
+__device__ __forceinline__ T rnd16(T x)
+{
+    if constexpr (R16 == 1)
+        return (T)__half2float(__float2half_rn((float)x));
+    else if constexpr (R16 == 2)
+        return (T)__bfloat162float(__float2bfloat16_rn((float)x));
+    else
+        return x;
+}
+
 // v = (J x J x J) in  (n^3 -> M^3); fin(q, value) receives each output.
-template <int NP, typename T, class Fin>
+template <int NP, typename T, int R16, class Fin>
 __device__ __forceinline__ void interp_fwd(const T *in, T *st1, T *st2, const T *sJ, Fin fin)
 {
     using C = ConvCfg<NP>;
@@ -171,7 +195,7 @@ __device__ __forceinline__ void interp_fwd(const T *in, T *st1, T *st2, const T 
         T s = 0;
 #pragma unroll
         for (int l = 0; l < NP; ++l) s = fma(sJ[q1 * NP + l], in[(k * NP + j) * NP + l], s);
-        st1[t] = s;
+        st1[t] = rnd16<R16>(s);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < C::T2; t += blockDim.x) {
@@ -179,7 +203,7 @@ __device__ __forceinline__ void interp_fwd(const T *in, T *st1, T *st2, const T 
         T s = 0;
 #pragma unroll
         for (int l = 0; l < NP; ++l) s = fma(sJ[q2 * NP + l], st1[(k * NP + l) * M + q1], s);
-        st2[t] = s;
+        st2[t] = rnd16<R16>(s);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < C::M3; t += blockDim.x) {
@@ -193,7 +217,7 @@ __device__ __forceinline__ void interp_fwd(const T *in, T *st1, T *st2, const T 
 }
 
 // out = (J^T x J^T x J^T) f  (M^3 -> n^3).
-template <int NP, typename T, class Fin>
+template <int NP, typename T, int R16, class Fin>
 __device__ __forceinline__ void interp_bwd(const T *f, T *st1, T *st2, const T *sJ, Fin fin)
 {
     using C = ConvCfg<NP>;
@@ -203,7 +227,7 @@ __device__ __forceinline__ void interp_bwd(const T *f, T *st1, T *st2, const T *
         T s = 0;
 #pragma unroll 4
         for (int q = 0; q < M; ++q) s = fma(sJ[q * NP + i], f[(q3 * M + q2) * M + q], s);
-        st2[t] = s;
+        st2[t] = rnd16<R16>(s);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < C::T1; t += blockDim.x) {  // [q3][j][i]
@@ -211,7 +235,7 @@ __device__ __forceinline__ void interp_bwd(const T *f, T *st1, T *st2, const T *
         T s = 0;
 #pragma unroll 4
         for (int q = 0; q < M; ++q) s = fma(sJ[q * NP + j], st2[(q3 * M + q) * NP + i], s);
-        st1[t] = s;
+        st1[t] = rnd16<R16>(s);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < C::N3; t += blockDim.x) {
@@ -224,7 +248,7 @@ __device__ __forceinline__ void interp_bwd(const T *f, T *st1, T *st2, const T *
     __syncthreads();
 }
 
-template <int NP, typename T>
+template <int NP, typename T, int R16>
 __global__ void __launch_bounds__(256) k_convect(ConvArgs a)
 {
     using C = ConvCfg<NP>;
@@ -238,17 +262,18 @@ __global__ void __launch_bounds__(256) k_convect(ConvArgs a)
     T *sJ = st2 + C::T2, *sD = sJ + M * NP, *seta = sD + NP * NP, *sw = seta + M;
     T *sc = sw + M;                       // trilinear coefficients [8][3]
     const T *D = (const T *)a.D, *tab = (const T *)a.tab;
-    for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sD[t] = D[t];
+    for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sD[t] = rnd16<R16>(D[t]);
     for (int t = threadIdx.x; t < M; t += blockDim.x) {
         seta[t] = tab[t];
         sw[t] = tab[M + t];
     }
-    for (int t = threadIdx.x; t < M * NP; t += blockDim.x) sJ[t] = tab[2 * M + t];
+    for (int t = threadIdx.x; t < M * NP; t += blockDim.x) sJ[t] = rnd16<R16>(tab[2 * M + t]);
     const T *jinv = (const T *)a.jinv;
     for (int64_t e = blockIdx.x; e < a.E; e += gridDim.x) {
         __syncthreads();
         const int64_t off = e * N3;
-        for (int t = threadIdx.x; t < 3 * N3; t += blockDim.x) su[t] = (T)a.u[t / N3][off + t % N3];
+        for (int t = threadIdx.x; t < 3 * N3; t += blockDim.x)
+            su[t] = rnd16<R16>((T)a.u[t / N3][off + t % N3]);
         if (threadIdx.x < 24) {  // x = c0 + c1 r + c2 s + c3 t + c4 rs + c5 rt + c6 st + c7 rst
             const int m = threadIdx.x / 3, d = threadIdx.x % 3;
             const int ex = (int)(e % a.nelx), ey = (int)((e / a.nelx) % a.nely),
@@ -267,7 +292,7 @@ __global__ void __launch_bounds__(256) k_convect(ConvArgs a)
         __syncthreads();
         // fine-grid velocity, scaled by the quadrature weight and |J|
         for (int d = 0; d < 3; ++d)
-            interp_fwd<NP, T>(su + d * N3, st1, st2, sJ, [&](int q, T v) { sfu[d * M3 + q] = v; });
+            interp_fwd<NP, T, R16>(su + d * N3, st1, st2, sJ, [&](int q, T v) { sfu[d * M3 + q] = v; });
         for (int q = threadIdx.x; q < M3; q += blockDim.x) {
             const int q1 = q % M, q2 = (q / M) % M, q3 = q / (M * M);
             const T r = seta[q1], s = seta[q2], t = seta[q3];
@@ -282,9 +307,9 @@ __global__ void __launch_bounds__(256) k_convect(ConvArgs a)
                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
             const T wd = sw[q1] * sw[q2] * sw[q3] * det;
-            sfu[q] *= wd;
-            sfu[M3 + q] *= wd;
-            sfu[2 * M3 + q] *= wd;
+            sfu[q] = rnd16<R16>(sfu[q] * wd);
+            sfu[M3 + q] = rnd16<R16>(sfu[M3 + q] * wd);
+            sfu[2 * M3 + q] = rnd16<R16>(sfu[2 * M3 + q] * wd);
         }
         __syncthreads();
         for (int c = 0; c < 3; ++c) {
@@ -300,18 +325,27 @@ __global__ void __launch_bounds__(256) k_convect(ConvArgs a)
                     gt = fma(sD[k * NP + l], uc[(l * NP + j) * NP + i], gt);
                 }
                 const T *ji = jinv + e * 9 * N3 + pn;
+                gr = rnd16<R16>(gr);
+                gs = rnd16<R16>(gs);
+                gt = rnd16<R16>(gt);
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
-                    sg[d * N3 + pn] = ji[(0 * 3 + d) * N3] * gr + ji[(1 * 3 + d) * N3] * gs +
-                                      ji[(2 * 3 + d) * N3] * gt;
+                    sg[d * N3 + pn] = rnd16<R16>(rnd16<R16>(ji[(0 * 3 + d) * N3]) * gr +
+                                                 rnd16<R16>(ji[(1 * 3 + d) * N3]) * gs +
+                                                 rnd16<R16>(ji[(2 * 3 + d) * N3]) * gt);
             }
             for (int q = threadIdx.x; q < M3; q += blockDim.x) sf[q] = 0;
             __syncthreads();
             for (int d = 0; d < 3; ++d)
-                interp_fwd<NP, T>(sg + d * N3, st1, st2, sJ,
-                                  [&](int q, T v) { sf[q] = fma(sfu[d * M3 + q], v, sf[q]); });
+                interp_fwd<NP, T, R16>(sg + d * N3, st1, st2, sJ,
+                                  [&](int q, T v) { sf[q] = fma(sfu[d * M3 + q], rnd16<R16>(v), sf[q]); });
+            if (R16) {
+                __syncthreads();
+                for (int q = threadIdx.x; q < M3; q += blockDim.x) sf[q] = rnd16<R16>(sf[q]);
+                __syncthreads();
+            }
             double *Cc = a.C[c] + off;
-            interp_bwd<NP, T>(sf, st1, st2, sJ, [&](int pn, T v) { Cc[pn] = (double)v; });
+            interp_bwd<NP, T, R16>(sf, st1, st2, sJ, [&](int pn, T v) { Cc[pn] = (double)v; });
         }
     }
 }
@@ -567,6 +601,19 @@ static size_t conv_smem(bool f32)
     return f32 ? ConvCfg<NP>::template smem<float>() : ConvCfg<NP>::template smem<double>();
 }
 
+template <int NP, typename T, int R16>
+static int run_convect(const ConvArgs &a, int grid, size_t smem, cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        SEM_CUDA(cudaFuncSetAttribute(k_convect<NP, T, R16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    k_convect<NP, T, R16><<<grid, 256, smem, s>>>(a);
+    SEM_CHECK_LAUNCH();
+    return SEM_OK;
+}
+
 template <int NP>
 static int launch_convect(sem_tgv *T, const double *const u[3], double *const C[3], cudaStream_t s)
 {
@@ -588,23 +635,31 @@ static int launch_convect(sem_tgv *T, const double *const u[3], double *const C[
         a.jinv = c->jinv32;
         a.D = c->tab32 + 2 * c->n;
         a.tab = T->tab32;
-        static bool attr = false;
-        if (!attr) {
-            SEM_CUDA(cudaFuncSetAttribute(k_convect<NP, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
-        }
-        k_convect<NP, float><<<grid, 256, smem, s>>>(a);
-    } else {
-        a.jinv = c->jinv64;
-        a.D = c->tab64 + 2 * c->n;
-        a.tab = T->tab64;
-        static bool attr = false;
-        if (!attr) {
-            SEM_CUDA(cudaFuncSetAttribute(k_convect<NP, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
-        }
-        k_convect<NP, double><<<grid, 256, smem, s>>>(a);
+        if (T->op == SEM_F16_TC)
+            return run_convect<NP, float, 1>(a, grid, smem, s);
+        if (T->op == SEM_BF16_TC)
+            return run_convect<NP, float, 2>(a, grid, smem, s);
+        return run_convect<NP, float, 0>(a, grid, smem, s);
     }
+    a.jinv = c->jinv64;
+    a.D = c->tab64 + 2 * c->n;
+    a.tab = T->tab64;
+    return run_convect<NP, double, 0>(a, grid, smem, s);
+}
+
+// Round the FP64 values of a[0..n) to FP32 values (FP32 storage numerics).
+__global__ void k_round_f32(double *__restrict__ a, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x)
+        a[t] = (double)__double2float_rn(a[t]);
+}
+
+static int round_stored(sem_tgv *T, double *a, int64_t n, cudaStream_t s)
+{
+    if (T->storage != SEM_F32) return SEM_OK;
+    const int64_t blocks = sem_ceil_div(n, 256);
+    k_round_f32<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(a, n);
     SEM_CHECK_LAUNCH();
     return SEM_OK;
 }
@@ -662,8 +717,10 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     const size_t bytes = sizeof(double) * nL;
     const Coef k = coef(q, T->dt);
     int rc;
-    // 1. convective term of the current velocity
+    // 1. convective term of the current velocity (stored: C history)
     rc = convect(T, T->u[0], T->C[0], s);
+    if (rc) return rc;
+    rc = round_stored(T, T->C[0][0], 3 * nL, s);
     if (rc) return rc;
     // 2. extrapolated convection
     k_tgv_F<<<(unsigned)sem_ceil_div(nL, 256), 256, 0, s>>>(
@@ -690,6 +747,8 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     rc = sem_dssum_dev(c, T->bp, SEM_F64, s);
     if (rc) return rc;
     rc = sem_pcg_solve_dev(c, 0, T->bp, T->p, 1.0, 0.0, T->po, s);
+    if (rc) return rc;
+    rc = round_stored(T, T->p, nL, s);
     if (rc) return rc;
     int io, so;
     const char *st0 = (const char *)sem_solve_state_ptr(c, 0, &io, &so);
@@ -732,6 +791,8 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
         SEM_CUDA(cudaMemcpyAsync(T->C[2][cc], T->C[1][cc], bytes, cudaMemcpyDeviceToDevice, s));
         SEM_CUDA(cudaMemcpyAsync(T->C[1][cc], T->C[0][cc], bytes, cudaMemcpyDeviceToDevice, s));
     }
+    rc = round_stored(T, T->u[0][0], 3 * nL, s);  // the new velocity
+    if (rc) return rc;
     return diag(T, 1, s);
 }
 
@@ -768,6 +829,11 @@ extern "C" int sem_tgv_init(sem_ctx *c, double nu, double dt, sem_dtype op, cons
     if (vel) T->vo = *vel;
     if (pres) T->po = *pres;
     if (op == SEM_F32 && !pres) T->po.inner = SEM_F32;
+    T->storage = SEM_F64;
+    T->op0 = op;
+    T->vin0 = T->vo.inner;
+    T->pin0 = T->po.inner;
+    T->cur_rule = -1;
     const int n = c->n;
     T->M = (3 * n + 1) / 2;
     const int64_t nL = c->nL;
@@ -869,6 +935,58 @@ extern "C" int sem_tgv_set(sem_tgv *T, int level, const double *u, const double 
     return SEM_OK;
 }
 
+static bool conv_dtype_ok(sem_dtype d)
+{
+    return d == SEM_F64 || d == SEM_F32 || d == SEM_F16_TC || d == SEM_BF16_TC;
+}
+
+static bool solve_dtype_ok(sem_dtype d)
+{
+    return d == SEM_F64 || d == SEM_F64_NATIVE || d == SEM_F32 || d == SEM_F16_TC || d == SEM_BF16_TC;
+}
+
+extern "C" int sem_tgv_set_policy(sem_tgv *T, int n, const sem_tgv_policy *rules)
+{
+    if (!T || n < 0 || n > SEM_TGV_MAX_RULES || (n > 0 && !rules)) return SEM_ERR_ARG;
+    for (int r = 0; r < n; ++r) {
+        const sem_tgv_policy &p = rules[r];
+        if (!conv_dtype_ok(p.sem) || !solve_dtype_ok(p.vel) || !solve_dtype_ok(p.pres) ||
+            (p.storage != SEM_F64 && p.storage != SEM_F32))
+            return SEM_ERR_ARG;
+        if (r > 0 && p.first_step < rules[r - 1].first_step) return SEM_ERR_ARG;
+    }
+    for (int r = 0; r < n; ++r) T->rules[r] = rules[r];
+    T->nrules = n;
+    T->cur_rule = -2;  // re-applied before the next step
+    return SEM_OK;
+}
+
+// Put the rule in force at step `step` (1-based) into effect; a change drops
+// the captured step graph so that the next steady step is captured again.
+static void apply_policy(sem_tgv *T, int step)
+{
+    int r = -1;
+    for (int k = 0; k < T->nrules; ++k)
+        if (T->rules[k].first_step <= step) r = k;
+    if (r == T->cur_rule) return;
+    if (r < 0) {
+        T->op = T->op0;
+        T->vo.inner = T->vin0;
+        T->po.inner = T->pin0;
+        T->storage = SEM_F64;
+    } else {
+        T->op = T->rules[r].sem;
+        T->vo.inner = T->rules[r].vel;
+        T->po.inner = T->rules[r].pres;
+        T->storage = T->rules[r].storage;
+    }
+    if (T->graph_state == 1) {
+        cudaGraphExecDestroy(T->graph);
+        T->graph_state = 0;
+    }
+    T->cur_rule = r;
+}
+
 extern "C" int sem_tgv_step(sem_tgv *T, int nsteps, sem_tgv_diag *out, void *stream)
 {
     if (!T || nsteps < 0) return SEM_ERR_ARG;
@@ -880,6 +998,7 @@ extern "C" int sem_tgv_step(sem_tgv *T, int nsteps, sem_tgv_diag *out, void *str
     for (int it = 0; it < nsteps; ++it) {
         const int q = T->step + 1 < 3 ? T->step + 1 : 3;
         int rc;
+        apply_policy(T, T->step + 1);
         if (q == 3 && s != 0 && T->graph_state == 0) {
             // capture one steady-state step; fall back to direct launches if capture fails
             cudaGraph_t g = nullptr;

@@ -1,0 +1,150 @@
+"""Precision policies of the Taylor-Green stepper: the configurations of Table 2.
+
+The paper's three-level model (Sec. 2, Fig. 2) maps (block, role, kernel, step
+range) to a precision under a global cap rp.  The stepper exposes it through
+``sem_tgv_set_policy``: per rule, the compute precision of the SEM block (the
+dealiased convection), of the velocity block (three Helmholtz solves) and of
+the pressure block (the Poisson solve), the storage cap, and the step the rule
+starts at.  Accumulation (dots, norms, refinement residuals, BDF/EXT sums,
+diagnostics) is FP64 in every configuration.
+
+Readings of Table 2 on this stepper:
+  - "fp32 compute" of a solve block: FP32 inner PCG inside FP64 iterative
+    refinement to the block's own tolerance; "fp64 compute": PCG on the
+    FP64-accurate operator;
+  - the SEM block's compute precision applies to the dealiased convection (its
+    hotspot, Fig. 3); the pointwise right-hand-side, divergence and gradient
+    kernels stay FP64;
+  - rp = fp32 (Group B): the stored state (velocity and convection histories,
+    pressure) is rounded to FP32 values each step;
+  - kernel-level fp16 overrides: adv_dealias = every operand of the convection's
+    contractions rounded to FP16 with FP32 accumulation (B-5); ax_helm = the
+    16-bit tensor-core operator in the inner PCG of the velocity (B-6) or the
+    pressure (B-7) block.
+
+Error metrics (Sec. 4.2, without the x100 %): e_E,max, e_Omega,max and
+e_Omega,peak of a run's KE / enstrophy history against a reference history.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_A = dict(storage="f64")
+_B = dict(storage="f32")
+
+TABLE2 = {
+    "A-0": dict(sem="f64", vel="f64", pres="f64", **_A),
+    "A-1": dict(sem="f32", vel="f32", pres="f32", **_A),
+    "A-2": dict(sem="f32", vel="f64", pres="f64", **_A),
+    "A-3": dict(sem="f64", vel="f32", pres="f64", **_A),
+    "A-4": dict(sem="f64", vel="f64", pres="f32", **_A),
+    "B-0": dict(sem="f32", vel="f32", pres="f32", **_B),
+    "B-1": dict(sem="f64", vel="f64", pres="f64", **_B),
+    "B-2": dict(sem="f64", vel="f32", pres="f32", **_B),
+    "B-3": dict(sem="f32", vel="f64", pres="f32", **_B),
+    "B-4": dict(sem="f32", vel="f32", pres="f64", **_B),
+    "B-5": dict(sem="f16_tc", vel="f32", pres="f32", **_B),
+    "B-6": dict(sem="f32", vel="f16_tc", pres="f32", **_B),
+    "B-7": dict(sem="f32", vel="f32", pres="f16_tc", **_B),
+}
+
+
+def rule(name: str, first_step: int = 1) -> dict:
+    """The Table 2 configuration `name` as a policy rule starting at first_step."""
+    return dict(TABLE2[name], first_step=first_step)
+
+
+def e_max(hist, ref) -> float:
+    """max_i |h_i - r_i| / max_i |r_i| (e_E,max and e_Omega,max of Sec. 4.2)."""
+    h, r = np.asarray(hist, dtype=float), np.asarray(ref, dtype=float)
+    return float(np.abs(h - r).max() / np.abs(r).max())
+
+
+def e_peak(hist, ref) -> float:
+    """|max_i h_i - max_i r_i| / max_i |r_i| (e_Omega,peak of Sec. 4.2)."""
+    h, r = np.asarray(hist, dtype=float), np.asarray(ref, dtype=float)
+    return float(abs(h.max() - r.max()) / np.abs(r).max())
+
+
+def replay(configs=None, nel=32, N=7, re=1600.0, dt=1e-3, steps=200, warm=3, maxit=4000):
+    """Run each configuration from the same initial state on cuda:0; returns a
+    list of dicts with ms/step of the timed steps (CUDA events around the
+    graph replays and one copy of the stepper's log), mean velocity / pressure
+    iterations, the worst status and the error metrics of its KE / enstrophy
+    history against A-0's.  The first `warm`
+    steps (startup orders and the graph capture) are part of the history but
+    not of the timing; a configuration whose solves fail to converge within
+    maxit iterations during them stops there (its row keeps the status)."""
+    import math
+
+    import torch
+
+    from . import inputs, sem
+
+    configs = list(configs or TABLE2)
+    if "A-0" not in configs:
+        configs = ["A-0"] + configs
+    dev = torch.device("cuda:0")
+    ctx = sem.Ctx(N, (nel,) * 3, (2 * math.pi,) * 3, (1, 1, 1))
+    xyz = torch.empty(3 * ctx.nL, dtype=torch.float64, device=dev)
+    ctx.coords(xyz)
+    x, y, z = xyz.view(3, -1)
+    ic = [t.contiguous() for t in inputs.tgv_initial(x, y, z, lib=torch)]
+    ic[2] = (ic[2] + 0 * x).contiguous()
+    vo = sem.opts(tol=1e-6, abs_tol=True, maxit=maxit)
+    po = sem.opts(tol=1e-4, abs_tol=True, maxit=maxit)
+    out, ref = [], None
+    for name in configs:
+        T = sem.TGV(ctx, 1.0 / re, dt, op="f64", vel=vo, pres=po)
+        T.set_policy([rule(name)])
+        T.set(*ic)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            d = T.step(warm, stream=stream)
+            ms = float("nan")
+            if all(r["status"] == 0 for r in d):  # a solve that fails to converge ends the run
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                d += T.step(steps - warm, stream=stream)  # ends with one copy of the device log
+                e1.record(stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1) / max(1, steps - warm)
+        ke = [r["ke"] for r in d]
+        en = [r["enstrophy"] for r in d]
+        row = dict(config=name, **TABLE2[name], ms_per_step=ms,
+                   vel_iters=float(np.mean([sum(r["iters"][1:]) / 3 for r in d])),
+                   pres_iters=float(np.mean([r["iters"][0] for r in d])),
+                   status=max((r["status"] for r in d), key=abs), ke=ke, enstrophy=en)
+        if name == "A-0":
+            ref = row
+        out.append(row)
+        T.close()
+    for row in out:
+        n = len(row["ke"])
+        row["steps"] = n
+        row["e_E_max"] = e_max(row["ke"], ref["ke"][:n])
+        row["e_Omega_max"] = e_max(row["enstrophy"], ref["enstrophy"][:n])
+        row["e_Omega_peak"] = e_peak(row["enstrophy"], ref["enstrophy"][:n])
+    return out
+
+
+def main(argv=None):
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--nel", type=int, default=32)
+    ap.add_argument("--N", type=int, default=7)
+    ap.add_argument("--re", type=float, default=1600.0)
+    ap.add_argument("--dt", type=float, default=1e-3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--configs", default=",".join(TABLE2))
+    args = ap.parse_args(argv)
+    rows = replay(args.configs.split(","), args.nel, args.N, args.re, args.dt, args.steps)
+    for r in rows:
+        r = {k: v for k, v in r.items() if k not in ("ke", "enstrophy")}
+        print(json.dumps(r))
+
+
+if __name__ == "__main__":
+    main()

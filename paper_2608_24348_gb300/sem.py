@@ -55,6 +55,11 @@ class SolveInfo(ctypes.Structure):
                 "rnorm": self.final_rnorm, "bnorm": self.bnorm}
 
 
+class TgvPolicy(ctypes.Structure):
+    _fields_ = [("first_step", ctypes.c_int), ("sem", ctypes.c_int), ("vel", ctypes.c_int),
+                ("pres", ctypes.c_int), ("storage", ctypes.c_int)]
+
+
 class TgvDiag(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("ke", ctypes.c_double), ("enstrophy", ctypes.c_double),
                 ("iters", ctypes.c_int * 4), ("status", ctypes.c_int)]
@@ -64,7 +69,8 @@ EXPORTS = ["sem_setup", "sem_destroy", "sem_get_info", "sem_strerror", "sem_coor
            "sem_ax", "sem_dssum", "sem_jacobi", "sem_solve_opts_default", "sem_pcg_solve",
            "sem_last_solve_info", "sem_pcg_solve_batched", "sem_tgv_init", "sem_tgv_set",
            "sem_tgv_step", "sem_tgv_get", "sem_tgv_energy", "sem_tgv_destroy",
-           "sem_pcg_solve_noalloc", "sem_device_status", "sem_tune_ax", "sem_set_ax_variant"]
+           "sem_pcg_solve_noalloc", "sem_device_status", "sem_tune_ax", "sem_set_ax_variant",
+           "sem_tgv_set_policy"]
 
 
 def lib_path() -> str:
@@ -113,6 +119,7 @@ def load(build_if_missing: bool = True):
         L.sem_tgv_get.argtypes = [vp, vp, vp, vp, vp, vp]
         L.sem_tgv_energy.argtypes = [vp, dp, dp, vp]
         L.sem_tgv_destroy.argtypes = [vp]
+        L.sem_tgv_set_policy.argtypes = [vp, ctypes.c_int, ctypes.POINTER(TgvPolicy)]
         L.sem_tgv_destroy.restype = None
         L.sem_pcg_solve_noalloc.argtypes = [ctypes.c_int] * 4 + [ip, vp, vp, vp, ctypes.c_double,
                                                                  ctypes.c_double,
@@ -339,6 +346,17 @@ class TGV:
         _check(_lib.sem_tgv_init(ctx.handle, float(nu), float(dt), DTYPES[op], ctypes.byref(vo),
                                  ctypes.byref(po), ctypes.byref(h)), "sem_tgv_init")
         self._h = h
+
+    def set_policy(self, rules):
+        """Precision schedule: a list of dicts with keys first_step (default 1),
+        sem, vel, pres, storage (names of DTYPES; defaults f64); [] restores the
+        precisions given at construction."""
+        arr = (TgvPolicy * max(1, len(rules)))()
+        for k, r in enumerate(rules):
+            arr[k] = TgvPolicy(int(r.get("first_step", 1)), DTYPES[r.get("sem", "f64")],
+                               DTYPES[r.get("vel", "f64")], DTYPES[r.get("pres", "f64")],
+                               DTYPES[r.get("storage", "f64")])
+        _check(_lib.sem_tgv_set_policy(self._h, len(rules), arr), "sem_tgv_set_policy")
 
     def set(self, u, v, w, p=None, level=0, step=0, t=0.0, stream=None):
         _check(_lib.sem_tgv_set(self._h, level, ptr(u), ptr(v), ptr(w), ptr(p), step, t,
