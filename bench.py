@@ -35,11 +35,13 @@ BYTES_F64 = 72  # read u 8 + G 48 + B 8, write w 8
 BYTES_F32 = 36
 FLOPS_PER_NODE = 12 * (N_ORDER + 1) + 21  # FP64 flops of one operator application per node
 # FP32-pipe operations per node of the folded FP64-accurate operator at N=7:
-# six folded contractions of 70 ops per output (4 compensated multiply-adds of
-# 12, a fold and a merge of 10, a normalisation of 2), the geometric step
-# (10 multiply-adds, 4 normalisations) and the final sums and weights
-# (profiles/sem_ax_dfeo_24cubed_N7.md measures 619 FMA-pipe ops per node)
-DF_OPS_PER_NODE = 6 * 70 + (10 * 12 + 4 * 2) + (2 * 8 + 2 * 12 + 3 * 2) + 4
+# six folded contractions of 48 ops per output (per half sum one exact product
+# of 4 and three compensated multiply-adds of 12; the un-normalised merge of 8
+# per output), three line folds of 8 per node before each contraction stage,
+# the geometric step (4 exact products, 6 multiply-adds), and the final sums,
+# weights and split of the FP64 join
+# (profiles/sem_ax_dfeo_24cubed_N7.md measures about 434 FMA-pipe ops per node)
+DF_OPS_PER_NODE = 6 * 48 + 2 * 3 * 8 + (4 * 4 + 6 * 12) + (2 * 8 + 4 + 12) + 2
 DF_KERNEL = "k_ax_dfeo<8>"
 # DRAM bytes per local node of k_ax_dfeo<8> from the ncu capture on the 24^3 mesh
 # (453.2 MB read + 47.0 MB written for 7,077,888 nodes), scaled to the 32^3 mesh
