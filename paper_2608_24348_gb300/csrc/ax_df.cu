@@ -4,18 +4,20 @@
 #include "common.cuh"
 #include "tma.cuh"
 
-// Thread 0 asks L2 for the u and geometry blocks of the next element group of
-// this block (elements [e0, e0 + ne) clipped to E), so that their loads find
-// them in L2 instead of waiting on HBM.
+// Thread 0 asks L2 for the geometry of this block's current element group
+// (read after the gradient stage, about half a group later) and for the u of
+// its next group (read at that group's start).  Elements are clipped to E.
+// Prefetching the next group's geometry as well (a whole group ahead) was
+// slower (0.468 vs 0.427 ms at 32^3, N=7) and L2 evicted a third of those
+// lines before use (37% more DRAM reads).
 template <int NP>
-__device__ __forceinline__ void df_prefetch_group(const double *u, const dfp *geo, int64_t e0, int ne,
-                                                  int64_t E)
+__device__ __forceinline__ void df_prefetch(const double *u, const dfp *geo, int64_t e0, int64_t en,
+                                            int ne, int64_t E)
 {
     constexpr int64_t NP3 = NP * NP * NP;
-    if (threadIdx.x != 0 || e0 >= E) return;
-    const int64_t e1 = e0 + ne < E ? e0 + ne : E;
-    l2_prefetch_span(u, e0 * NP3 * 8, e1 * NP3 * 8);
-    l2_prefetch_span(geo, e0 * 7 * NP3 * 8, e1 * 7 * NP3 * 8);
+    if (threadIdx.x != 0) return;
+    if (e0 < E) l2_prefetch_span(geo, e0 * 7 * NP3 * 8, (e0 + ne < E ? e0 + ne : E) * 7 * NP3 * 8);
+    if (en < E) l2_prefetch_span(u, en * NP3 * 8, (en + ne < E ? en + ne : E) * NP3 * 8);
 }
 
 template <int NP>
@@ -33,7 +35,7 @@ __global__ void __launch_bounds__(AxDfCfg<NP>::THREADS, 2)
     dfp *svr = su + C::NP3, *svs = svr + C::NP3;
     ax_df_load_D<NP>(D, sD, sDT);
     for (int64_t e0 = (int64_t)blockIdx.x * C::NE; e0 < E; e0 += (int64_t)gridDim.x * C::NE) {
-        df_prefetch_group<NP>(u, geo, e0 + (int64_t)gridDim.x * C::NE, C::NE, E);
+        df_prefetch<NP>(u, geo, e0, e0 + (int64_t)gridDim.x * C::NE, C::NE, E);
         const int64_t e = e0 + grp;
         const bool active = e < E;
         const int64_t off = (active ? e : 0) * C::NP3;
@@ -62,7 +64,7 @@ __global__ void __launch_bounds__(AxEoCfg<NP>::THREADS, 2)
     dfp *slab = sm + 4 * HH + (size_t)grp * 5 * C::SLAB;
     for (int t = threadIdx.x; t < 4 * HH; t += blockDim.x) stab[t] = tabs[t];
     for (int64_t e0 = (int64_t)blockIdx.x * C::NE; e0 < E; e0 += (int64_t)gridDim.x * C::NE) {
-        df_prefetch_group<NP>(u, geo, e0 + (int64_t)gridDim.x * C::NE, C::NE, E);
+        df_prefetch<NP>(u, geo, e0, e0 + (int64_t)gridDim.x * C::NE, C::NE, E);
         const int64_t e = e0 + grp;
         const bool active = e < E;
         const int64_t off = (active ? e : 0) * C::NP3;

@@ -157,6 +157,25 @@ __device__ __forceinline__ int64_t phase_items(const ProbDesc &P, int ph)
     }
 }
 
+// FP32 dot products accumulated on the FP32 pipes: every product exact
+// (TwoProd), every sum error-free (TwoSum), the errors gathered in A.e -- the
+// compensated dot product of Ogita, Rump & Oishi, as accurate as summing the
+// exact products in twice FP32 precision.  GB300 runs FP64 at 1/58 of the
+// FP32 rate, so the per-node FP64 multiply-add (and two conversions) this
+// replaces cost more issue time than the ten FP32 operations here.
+__device__ __forceinline__ void dot2_acc(dfacc &A, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float ep = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(A.s, p);
+    const float bv = __fsub_rn(s, A.s);
+    const float t = __fadd_rn(__fsub_rn(A.s, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+    A.s = s;
+    A.e = __fadd_rn(A.e, __fadd_rn(t, ep));
+}
+
+__device__ __forceinline__ double dfacc_value(dfacc A) { return (double)A.s + (double)A.e; }
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -248,11 +267,13 @@ __device__ __forceinline__ void elem_item(const ProbDesc &P, double alpha, doubl
             p[q] = pn;
             return (T)pn;
         };
+        dfacc dot = {0.f, 0.f};
         auto store = [&](int q, T v, T u) {
             w[q] = v;
-            acc = fma((double)u, (double)v, acc);
+            dot2_acc(dot, u, v);
         };
         ax_element<NP, T>(load, store, geo, (T)P.h1, (T)P.h2, sD, sDT, su, svr, svs, tid, active);
+        acc += dfacc_value(dot);
     }
 }
 
@@ -399,11 +420,13 @@ __device__ __forceinline__ void elem_item_tc(const ProbDesc &P, double alpha, do
         P.p32[q] = pn;
         return pn;
     };
+    dfacc dot = {0.f, 0.f};
     auto store = [&](int64_t q, float v, float u) {
         P.w32[q] = v;
-        acc = fma((double)u, (double)v, acc);
+        dot2_acc(dot, u, v);
     };
     ax_tc_group<NP>(load, store, P.geo32, P.D32, (float)P.h1, (float)P.h2, P.E, g, fp16, smem);
+    acc += dfacc_value(dot);
 }
 
 template <int NP, int MODE>
@@ -595,6 +618,7 @@ __device__ __forceinline__ void uniq_item(const ProbDesc &P, const PState &S, in
                 r0[r] = __ldcg(P.r + f);
                 mv[r] = __ldcg(P.minv32 + f);
             }
+            dfacc d0 = {0.f, 0.f}, d1 = {0.f, 0.f};
 #pragma unroll
             for (int r = 0; r < RU; ++r) {
                 if (!ok[r]) continue;
@@ -603,10 +627,11 @@ __device__ __forceinline__ void uniq_item(const ProbDesc &P, const PState &S, in
                     P.r32[cp] = rv;
                     P.d32[cp] = 0.0f;
                 });
-                const double rd = rv;
-                v[0] = fma(rd, rd, v[0]);
-                v[1] = fma(rd, (double)(mv[r] * rv), v[1]);
+                dot2_acc(d0, rv, rv);
+                dot2_acc(d1, rv, mv[r] * rv);
             }
+            v[0] += dfacc_value(d0);
+            v[1] += dfacc_value(d1);
         } break;
         case PH_C32: {
             float s[RU], r0[RU], mv[RU];
@@ -620,15 +645,17 @@ __device__ __forceinline__ void uniq_item(const ProbDesc &P, const PState &S, in
                 mv[r] = __ldcg(P.minv32 + f);
             }
             const float a = (float)S.alpha;
+            dfacc d0 = {0.f, 0.f}, d1 = {0.f, 0.f};
 #pragma unroll
             for (int r = 0; r < RU; ++r) {
                 if (!ok[r]) continue;
                 const float rv = r0[r] - a * s[r];
                 UQ_FOR_COPIES(R[r], mx, xo, P.r32[cp] = rv);
-                const double rd = rv;
-                v[0] = fma(rd, rd, v[0]);
-                v[1] = fma(rd, (double)(mv[r] * rv), v[1]);
+                dot2_acc(d0, rv, rv);
+                dot2_acc(d1, rv, mv[r] * rv);
             }
+            v[0] += dfacc_value(d0);
+            v[1] += dfacc_value(d1);
         } break;
         default: break;
     }
