@@ -42,6 +42,7 @@
 #include "ax_tc.cuh"
 #include "common.cuh"
 #include "gs.cuh"
+#include "tma.cuh"
 
 #define SEM_MAXP 64
 #define SEM_SOLVE_THREADS 256
@@ -51,6 +52,10 @@
 #endif
 #ifndef SEM_SOLVE_F32_MINB
 #define SEM_SOLVE_F32_MINB 3
+#endif
+// Element phases prefetch their group's geometric factors into L2.
+#ifndef SEM_SOLVE_GEO_PREFETCH
+#define SEM_SOLVE_GEO_PREFETCH 1
 #endif
 // FP64-accurate element phases of even orders use the folded operator.
 #ifndef SEM_SOLVE_DF_FOLDED
@@ -204,6 +209,20 @@ __device__ __forceinline__ void block_accumulate(double v[3], double *s_red, dou
     __syncthreads();
 }
 
+// Thread 0 asks L2 for the geometric factors of the element group this block
+// is about to work on (bytes [e0, e1) elements of a [E][7][NP^3] array of
+// `wb`-byte words): the operator reads them after its gradient stage, about
+// half an element phase later.  (A whole group ahead let L2 evict the element
+// phase's output before the gather read it.)
+template <int NP>
+__device__ __forceinline__ void geo_prefetch(const void *geo, int64_t e0, int ne, int64_t E, int wb)
+{
+    constexpr int64_t N3 = NP * NP * NP;
+    if (!SEM_SOLVE_GEO_PREFETCH || threadIdx.x != 0 || e0 >= E) return;
+    const int64_t e1 = e0 + ne < E ? e0 + ne : E;
+    l2_prefetch_span(geo, e0 * 7 * N3 * wb, e1 * 7 * N3 * wb);
+}
+
 // ---------------------------------------------------------------------------
 // element items
 // ---------------------------------------------------------------------------
@@ -228,6 +247,7 @@ __device__ __forceinline__ void elem_item(const ProbDesc &P, double alpha, doubl
     const int64_t off = (active ? e : 0) * C::NP3;
     const T *D = KIND == 2 ? (const T *)P.D32 : (const T *)P.D64;
     const T *geo = (KIND == 2 ? (const T *)P.geo32 : (const T *)P.geo64) + (active ? e : 0) * 7 * C::NP3;
+    if (KIND == 2) geo_prefetch<NP>(P.geo32, g * C::NE, C::NE, P.E, 4);  // (native FP64: no gain)
     ax_load_D<NP, T>(D, sD, sDT);
     if (KIND == 0) {
         const double *x = P.x + off;
@@ -298,6 +318,7 @@ __device__ __forceinline__ void elem_item_df(const ProbDesc &P, double alpha, do
     const dfp *geo = P.geodf + (active ? e : 0) * 7 * C::NP3;
     const float h1h = (float)P.h1, h2h = (float)P.h2;
     const dfp H1 = {h1h, (float)(P.h1 - (double)h1h)}, H2 = {h2h, (float)(P.h2 - (double)h2h)};
+    geo_prefetch<NP>(P.geodf, g * C::NE, C::NE, P.E, 8);
     ax_df_load_D<NP>(P.Ddf, sD, sDT);
     int *myexp = sexp + (inrange ? grp : 0);
     if (KIND == 0) {
@@ -355,6 +376,7 @@ __device__ __forceinline__ void elem_item_dfeo(const ProbDesc &P, double alpha, 
     const dfp *geo = P.geodf + (active ? e : 0) * 7 * C::NP3;
     const float h1h = (float)P.h1, h2h = (float)P.h2;
     const dfp H1 = {h1h, (float)(P.h1 - (double)h1h)}, H2 = {h2h, (float)(P.h2 - (double)h2h)};
+    geo_prefetch<NP>(P.geodf, g * C::NE, C::NE, P.E, 8);
     for (int t = threadIdx.x; t < 4 * HH; t += blockDim.x) stab[t] = P.Ddfeo[t];
     int *myexp = sexp + (inrange ? grp : 0);
     if (KIND == 0) {
