@@ -19,7 +19,9 @@
  *    argument: double for SEM_F64, float for the other three.
  *  - Field pointers may be device memory (the fast path) or host memory
  *    (pinned or pageable); host buffers are staged through device buffers
- *    owned by the context, allocated on the first such call.
+ *    owned by the context, allocated on the first such call (sem_ax also
+ *    creates two streams and a few events then, and overlaps the copies of
+ *    its element chunks with the operator on the other chunks).
  *  - The caller owns every field buffer.  The library owns the geometry and
  *    the solver workspaces; it allocates only in sem_setup, sem_tgv_init and
  *    the first host-pointer call, never inside a device-pointer hot call.
@@ -289,6 +291,18 @@ typedef struct {
  * re-captures the step graph.  Returns SEM_ERR_ARG for an unsupported
  * precision or an unsorted schedule (the previous schedule then stays). */
 SEM_API int sem_tgv_set_policy(sem_tgv *tgv, int n, const sem_tgv_policy *rules);
+
+/* Projection of the pressure solve onto previous solutions (Sec. 3: the
+ * pressure solver keeps a projection space of dimension 20; the A-conjugate
+ * projection of Fischer, CMAME 163, 1998).  max_vectors in 1..32 keeps an
+ * A-orthonormal basis of up to that many earlier pressure solutions: each
+ * pressure solve starts from the A-projection of its right-hand side onto the
+ * basis and iterates only on the remainder, whose solution (A-orthogonalised
+ * twice) joins the basis; a full basis restarts from the latest solution.
+ * 0 turns it off (the default).  Allocates 2 max_vectors + 5 FP64 E-vectors on
+ * the context's device (SEM_ERR_NOMEM if they do not fit); synchronises the
+ * device; the next step re-captures the step graph.  The basis starts empty. */
+SEM_API int sem_tgv_set_projection(sem_tgv *tgv, int max_vectors);
 
 /* Set the state at history level (0 = u^n, 1 = u^{n-1}, 2 = u^{n-2}) from
  * FP64 E-vectors u, v, w (and p for level 0; may be NULL); step is the number

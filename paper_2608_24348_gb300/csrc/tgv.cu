@@ -36,6 +36,7 @@ GsDesc sem_gs_desc(const sem_ctx *c);
 int sem_run_geometry(sem_ctx *c, double *xyz, bool with_jinv, cudaStream_t s);
 int sem_alloc_ws(sem_ctx *c, int slot);
 int sem_dssum_dev(sem_ctx *c, void *u, sem_dtype dt, cudaStream_t s);
+int sem_ax_dev(sem_ctx *c, const void *u, void *w, double h1, double h2, sem_dtype dt, cudaStream_t s);
 int sem_pcg_solve_dev(sem_ctx *c, int slot, const double *b, double *x, double h1, double h2,
                       const sem_solve_opts &o, cudaStream_t s);
 int sem_pcg_solve_dev_batch(sem_ctx *c, int np, const double *const *b, double *const *x, double h1,
@@ -66,6 +67,13 @@ struct sem_tgv {
     sem_dtype op0, vin0, pin0;  // the precisions given to sem_tgv_init
     sem_tgv_policy rules[SEM_TGV_MAX_RULES];
     int nrules, cur_rule;  // cur_rule: -1 = init precisions, -2 = not applied yet
+    // projection of the pressure solve (0 vectors = off)
+    int proj_max;
+    double *pX, *pBX;      // [proj_max][nL]: A-orthonormal basis and A times it (assembled)
+    double *pw, *pxb, *pbq, *pdx, *padx;  // 1/multiplicity, projection, remainder RHS, solve, A v
+    double *pcoef;         // device scalars: coefficients [TGV_PMAX], norms [2]
+    double *ppart;         // per-block partial dots [TGV_PBLK][TGV_PMAX]
+    int *pint;             // device ints: basis size L, 1, restart flag
     int step, M;
     double t;
     double *u[3][3], *C[3][3], *p, *unew[3], *F[3], *g[3], *bp, *rhs[3];
@@ -709,6 +717,9 @@ static int diag(sem_tgv *T, int advance, cudaStream_t s)
     return SEM_OK;
 }
 
+static int pressure_projected(sem_tgv *T, cudaStream_t s);
+static void proj_free(sem_tgv *T);
+
 // One step of order q on stream s (capturable).
 static int step_once(sem_tgv *T, int q, cudaStream_t s)
 {
@@ -746,7 +757,7 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     SEM_CHECK_LAUNCH();
     rc = sem_dssum_dev(c, T->bp, SEM_F64, s);
     if (rc) return rc;
-    rc = sem_pcg_solve_dev(c, 0, T->bp, T->p, 1.0, 0.0, T->po, s);
+    rc = T->proj_max > 0 ? pressure_projected(T, s) : sem_pcg_solve_dev(c, 0, T->bp, T->p, 1.0, 0.0, T->po, s);
     if (rc) return rc;
     rc = round_stored(T, T->p, nL, s);
     if (rc) return rc;
@@ -801,6 +812,7 @@ extern "C" void sem_tgv_destroy(sem_tgv *T)
     if (!T) return;
     cudaDeviceSynchronize();
     if (T->graph_state == 1) cudaGraphExecDestroy(T->graph);
+    proj_free(T);
     if (T->block) cudaFree(T->block);
     if (T->part) cudaFree(T->part);
     if (T->tab64) cudaFree(T->tab64);
@@ -932,6 +944,243 @@ extern "C" int sem_tgv_set(sem_tgv *T, int level, const double *u, const double 
         SEM_CHECK_LAUNCH();
     }
     SEM_CUDA(cudaStreamSynchronize(s));
+    return SEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Projection of the pressure solve onto previous solutions (Sec. 3: the
+// pressure solver keeps a projection space of dimension 20).  This is the
+// A-conjugate projection of Fischer (1998): with an A-orthonormal basis X of
+// earlier solutions and BX = A X,
+//     alpha = X^T b,  x_bar = X alpha,  b' = b - BX alpha,
+// the solve is for the remainder A dx = b', p = x_bar + dx, and dx (A-
+// orthogonalised twice against X, classical Gram-Schmidt, then A-normalised)
+// joins the basis; a full basis restarts from the latest solution p.  Inner
+// products are the assembled ones (local sums weighted by 1/multiplicity).
+// Everything stays on the device, so a captured step replays it.
+// ---------------------------------------------------------------------------
+
+#define TGV_PMAX 32   // largest basis
+#define TGV_PBLK 304  // blocks of the dot kernels (fixed: deterministic sums)
+
+// part[b][k] = block b's share of sum_i X_k[i] v[i] w[i], k < L (L = *Ld).
+__global__ void __launch_bounds__(256, 2) k_proj_dot(const double *__restrict__ X, const double *__restrict__ v,
+                                                  const double *__restrict__ w, const int *__restrict__ Ld,
+                                                  int64_t n, double *__restrict__ part)
+{
+    __shared__ double red[8][TGV_PMAX];
+    const int L = *Ld;
+    double acc[TGV_PMAX];
+#pragma unroll
+    for (int k = 0; k < TGV_PMAX; ++k) acc[k] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double t = v[i] * w[i];
+#pragma unroll
+        for (int k = 0; k < TGV_PMAX; ++k)
+            if (k < L) acc[k] = fma(__ldcg(X + (int64_t)k * n + i), t, acc[k]);
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < TGV_PMAX; ++k) {
+        if (k >= L) break;
+        double a = acc[k];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[wp][k] = a;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        double a = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += red[q][k];
+        part[(int64_t)blockIdx.x * TGV_PMAX + k] = a;
+    }
+}
+
+// c[k] = sum over blocks of part[b][k] in block order, k < L.
+__global__ void k_proj_dot_final(const double *__restrict__ part, const int *__restrict__ Ld,
+                                 double *__restrict__ c)
+{
+    const int L = *Ld, lane = threadIdx.x & 31;
+    for (int k = threadIdx.x >> 5; k < L; k += blockDim.x >> 5) {
+        double a = 0.0;
+        for (int b = lane; b < TGV_PBLK; b += 32) a += part[(int64_t)b * TGV_PMAX + k];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) c[k] = a;
+    }
+}
+
+// out[i] = (a ? a[i] : 0) + sg * sum_{k<L} c[k] X_k[i]  (out may alias a).
+__global__ void k_proj_axpy(double *out, const double *a, const double *__restrict__ X,
+                            const double *__restrict__ c, double sg, const int *__restrict__ Ld, int64_t n)
+{
+    const int L = *Ld;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < L; ++k) s = fma(c[k], __ldcg(X + (int64_t)k * n + i), s);
+        out[i] = fma(sg, s, a ? a[i] : 0.0);
+    }
+}
+
+__global__ void k_vec_add(double *out, const double *a, const double *b, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] + b[i];
+}
+
+// Before the update: a full basis restarts (L = 0) and the latest solution p
+// replaces dx as the vector to add.  pint = {L, 1, restart}.
+__global__ void k_proj_restart(int *pint, int Lmax)
+{
+    pint[2] = pint[0] >= Lmax;
+    if (pint[2]) pint[0] = 0;
+}
+
+__global__ void k_copy_if(double *dst, const double *src, const int *flag, int64_t n)
+{
+    if (!*flag) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// Append v / |v|_A and A v / |v|_A as basis vector L when the A-norm left after
+// the orthogonalisation is not round-off (nrm[1] > 1e-20 nrm[0], nrm[0] = the
+// A-norm squared before it).  The count is raised by k_proj_inc afterwards.
+__global__ void k_proj_append(double *X, double *BX, const double *v, const double *av,
+                              const double *nrm, const int *pint, int64_t n)
+{
+    const double n0 = nrm[0], n1 = nrm[1];
+    if (!(n1 > 1e-20 * n0) || !(n1 > 0.0)) return;
+    const int L = pint[0];
+    const double s = 1.0 / sqrt(n1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        X[(int64_t)L * n + i] = v[i] * s;
+        BX[(int64_t)L * n + i] = av[i] * s;
+    }
+}
+
+__global__ void k_proj_inc(int *pint, const double *nrm)
+{
+    if (nrm[1] > 1e-20 * nrm[0] && nrm[1] > 0.0) pint[0] += 1;
+}
+
+__global__ void k_recip_inplace(double *a, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = 1.0 / a[i];
+}
+
+__global__ void k_fill(double *a, double v, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+static unsigned vec_grid(int64_t n)
+{
+    const int64_t b = sem_ceil_div(n, 256);
+    return (unsigned)(b < 2048 ? b : 2048);
+}
+
+// c[0..L) = <X_k, v> (assembled), L from *Ld.
+static int proj_dot(sem_tgv *T, const double *X, const double *v, const int *Ld, double *c, cudaStream_t s)
+{
+    const int64_t n = T->c->nL;
+    k_proj_dot<<<TGV_PBLK, 256, 0, s>>>(X, v, T->pw, Ld, n, T->ppart);
+    SEM_CHECK_LAUNCH();
+    k_proj_dot_final<<<1, 1024, 0, s>>>(T->ppart, Ld, c);
+    SEM_CHECK_LAUNCH();
+    return SEM_OK;
+}
+
+static void proj_free(sem_tgv *T)
+{
+    double *ps[] = {T->pX, T->pBX, T->pw, T->pxb, T->pbq, T->pdx, T->padx, T->pcoef, T->ppart};
+    for (double *p : ps)
+        if (p) cudaFree(p);
+    if (T->pint) cudaFree(T->pint);
+    T->pX = T->pBX = T->pw = T->pxb = T->pbq = T->pdx = T->padx = T->pcoef = T->ppart = nullptr;
+    T->pint = nullptr;
+    T->proj_max = 0;
+}
+
+// The pressure solve of one step with projection (capturable): p from bp.
+static int pressure_projected(sem_tgv *T, cudaStream_t s)
+{
+    sem_ctx *c = T->c;
+    const int64_t n = c->nL;
+    const unsigned g = vec_grid(n);
+    int *L = T->pint, *one = T->pint + 1, *restart = T->pint + 2;
+    double *alpha = T->pcoef, *nrm = T->pcoef + TGV_PMAX;
+    int rc;
+    // projection of the new right-hand side
+    if ((rc = proj_dot(T, T->pX, T->bp, L, alpha, s))) return rc;
+    k_proj_axpy<<<g, 256, 0, s>>>(T->pxb, nullptr, T->pX, alpha, 1.0, L, n);
+    k_proj_axpy<<<g, 256, 0, s>>>(T->pbq, T->bp, T->pBX, alpha, -1.0, L, n);
+    SEM_CHECK_LAUNCH();
+    // the remainder, from a zero guess
+    SEM_CUDA(cudaMemsetAsync(T->pdx, 0, sizeof(double) * n, s));
+    if ((rc = sem_pcg_solve_dev(c, 0, T->pbq, T->pdx, 1.0, 0.0, T->po, s))) return rc;
+    k_vec_add<<<g, 256, 0, s>>>(T->p, T->pxb, T->pdx, n);
+    SEM_CHECK_LAUNCH();
+    // basis update: v = dx (or p after a restart), A v, CGS twice, A-normalise, append
+    k_proj_restart<<<1, 1, 0, s>>>(T->pint, T->proj_max);
+    k_copy_if<<<g, 256, 0, s>>>(T->pdx, T->p, restart, n);
+    SEM_CHECK_LAUNCH();
+    if ((rc = sem_ax_dev(c, T->pdx, T->padx, 1.0, 0.0, SEM_F64, s))) return rc;
+    if ((rc = sem_dssum_dev(c, T->padx, SEM_F64, s))) return rc;
+    k_proj_dot<<<TGV_PBLK, 256, 0, s>>>(T->pdx, T->padx, T->pw, one, n, T->ppart);
+    k_proj_dot_final<<<1, 1024, 0, s>>>(T->ppart, one, nrm);
+    SEM_CHECK_LAUNCH();
+    for (int pass = 0; pass < 2; ++pass) {
+        if ((rc = proj_dot(T, T->pBX, T->pdx, L, alpha, s))) return rc;
+        k_proj_axpy<<<g, 256, 0, s>>>(T->pdx, T->pdx, T->pX, alpha, -1.0, L, n);
+        k_proj_axpy<<<g, 256, 0, s>>>(T->padx, T->padx, T->pBX, alpha, -1.0, L, n);
+        SEM_CHECK_LAUNCH();
+    }
+    k_proj_dot<<<TGV_PBLK, 256, 0, s>>>(T->pdx, T->padx, T->pw, one, n, T->ppart);
+    k_proj_dot_final<<<1, 1024, 0, s>>>(T->ppart, one, nrm + 1);
+    k_proj_append<<<g, 256, 0, s>>>(T->pX, T->pBX, T->pdx, T->padx, nrm, T->pint, n);
+    k_proj_inc<<<1, 1, 0, s>>>(T->pint, nrm);
+    SEM_CHECK_LAUNCH();
+    return SEM_OK;
+}
+
+extern "C" int sem_tgv_set_projection(sem_tgv *T, int max_vectors)
+{
+    if (!T || max_vectors < 0 || max_vectors > TGV_PMAX) return SEM_ERR_ARG;
+    SEM_CUDA(cudaDeviceSynchronize());
+    proj_free(T);
+    if (T->graph_state == 1) {
+        cudaGraphExecDestroy(T->graph);
+        T->graph_state = 0;
+    }
+    if (max_vectors == 0) return SEM_OK;
+    sem_ctx *c = T->c;
+    const int64_t n = c->nL;
+    const size_t vb = sizeof(double) * (size_t)n;
+    bool ok = cudaMalloc(&T->pX, vb * max_vectors) == cudaSuccess &&
+              cudaMalloc(&T->pBX, vb * max_vectors) == cudaSuccess &&
+              cudaMalloc(&T->pw, vb) == cudaSuccess && cudaMalloc(&T->pxb, vb) == cudaSuccess &&
+              cudaMalloc(&T->pbq, vb) == cudaSuccess && cudaMalloc(&T->pdx, vb) == cudaSuccess &&
+              cudaMalloc(&T->padx, vb) == cudaSuccess &&
+              cudaMalloc(&T->pcoef, sizeof(double) * (TGV_PMAX + 2)) == cudaSuccess &&
+              cudaMalloc(&T->ppart, sizeof(double) * TGV_PBLK * TGV_PMAX) == cudaSuccess &&
+              cudaMalloc(&T->pint, sizeof(int) * 4) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        proj_free(T);
+        return SEM_ERR_NOMEM;
+    }
+    const int h[4] = {0, 1, 0, 0};
+    SEM_CUDA(cudaMemcpy(T->pint, h, sizeof(h), cudaMemcpyHostToDevice));
+    // weights 1/multiplicity: dssum of ones
+    k_fill<<<vec_grid(n), 256>>>(T->pw, 1.0, n);
+    SEM_CHECK_LAUNCH();
+    int rc = sem_dssum_dev(c, T->pw, SEM_F64, 0);
+    if (rc) return rc;
+    k_recip_inplace<<<vec_grid(n), 256>>>(T->pw, n);
+    SEM_CHECK_LAUNCH();
+    SEM_CUDA(cudaDeviceSynchronize());
+    T->proj_max = max_vectors;
     return SEM_OK;
 }
 

@@ -66,7 +66,7 @@ def e_peak(hist, ref) -> float:
     return float(abs(h.max() - r.max()) / np.abs(r).max())
 
 
-def replay(configs=None, nel=32, N=7, re=1600.0, dt=1e-3, steps=200, warm=3, maxit=4000):
+def replay(configs=None, nel=32, N=7, re=1600.0, dt=1e-3, steps=200, warm=3, maxit=4000, projection=0):
     """Run each configuration from the same initial state on cuda:0; returns a
     list of dicts with ms/step of the timed steps (CUDA events around the
     graph replays and one copy of the stepper's log), mean velocity / pressure
@@ -74,7 +74,9 @@ def replay(configs=None, nel=32, N=7, re=1600.0, dt=1e-3, steps=200, warm=3, max
     history against A-0's.  The first `warm`
     steps (startup orders and the graph capture) are part of the history but
     not of the timing; a configuration whose solves fail to converge within
-    maxit iterations during them stops there (its row keeps the status)."""
+    maxit iterations during them stops there (its row keeps the status).
+    projection > 0 keeps that many earlier pressure solutions for the
+    projection of each pressure solve (Sec. 3 uses 20)."""
     import math
 
     import torch
@@ -97,6 +99,8 @@ def replay(configs=None, nel=32, N=7, re=1600.0, dt=1e-3, steps=200, warm=3, max
     for name in configs:
         T = sem.TGV(ctx, 1.0 / re, dt, op="f64", vel=vo, pres=po)
         T.set_policy([rule(name)])
+        if projection:
+            T.set_projection(projection)
         T.set(*ic)
         stream = torch.cuda.Stream()
         with torch.cuda.stream(stream):
@@ -111,7 +115,7 @@ def replay(configs=None, nel=32, N=7, re=1600.0, dt=1e-3, steps=200, warm=3, max
                 ms = e0.elapsed_time(e1) / max(1, steps - warm)
         ke = [r["ke"] for r in d]
         en = [r["enstrophy"] for r in d]
-        row = dict(config=name, **TABLE2[name], ms_per_step=ms,
+        row = dict(config=name, **TABLE2[name], projection=projection, ms_per_step=ms,
                    vel_iters=float(np.mean([sum(r["iters"][1:]) / 3 for r in d])),
                    pres_iters=float(np.mean([r["iters"][0] for r in d])),
                    status=max((r["status"] for r in d), key=abs), ke=ke, enstrophy=en)
@@ -139,8 +143,10 @@ def main(argv=None):
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--configs", default=",".join(TABLE2))
+    ap.add_argument("--projection", type=int, default=0)
     args = ap.parse_args(argv)
-    rows = replay(args.configs.split(","), args.nel, args.N, args.re, args.dt, args.steps)
+    rows = replay(args.configs.split(","), args.nel, args.N, args.re, args.dt, args.steps,
+                  projection=args.projection)
     for r in rows:
         r = {k: v for k, v in r.items() if k not in ("ke", "enstrophy")}
         print(json.dumps(r))

@@ -70,7 +70,7 @@ EXPORTS = ["sem_setup", "sem_destroy", "sem_get_info", "sem_strerror", "sem_coor
            "sem_last_solve_info", "sem_pcg_solve_batched", "sem_tgv_init", "sem_tgv_set",
            "sem_tgv_step", "sem_tgv_get", "sem_tgv_energy", "sem_tgv_destroy",
            "sem_pcg_solve_noalloc", "sem_device_status", "sem_tune_ax", "sem_set_ax_variant",
-           "sem_tgv_set_policy"]
+           "sem_tgv_set_policy", "sem_tgv_set_projection"]
 
 
 def lib_path() -> str:
@@ -120,6 +120,7 @@ def load(build_if_missing: bool = True):
         L.sem_tgv_energy.argtypes = [vp, dp, dp, vp]
         L.sem_tgv_destroy.argtypes = [vp]
         L.sem_tgv_set_policy.argtypes = [vp, ctypes.c_int, ctypes.POINTER(TgvPolicy)]
+        L.sem_tgv_set_projection.argtypes = [vp, ctypes.c_int]
         L.sem_tgv_destroy.restype = None
         L.sem_pcg_solve_noalloc.argtypes = [ctypes.c_int] * 4 + [ip, vp, vp, vp, ctypes.c_double,
                                                                  ctypes.c_double,
@@ -357,6 +358,10 @@ class TGV:
                                DTYPES[r.get("vel", "f64")], DTYPES[r.get("pres", "f64")],
                                DTYPES[r.get("storage", "f64")])
         _check(_lib.sem_tgv_set_policy(self._h, len(rules), arr), "sem_tgv_set_policy")
+
+    def set_projection(self, max_vectors):
+        """Keep up to max_vectors earlier pressure solutions for projection (0 = off)."""
+        _check(_lib.sem_tgv_set_projection(self._h, int(max_vectors)), "sem_tgv_set_projection")
 
     def set(self, u, v, w, p=None, level=0, step=0, t=0.0, stream=None):
         _check(_lib.sem_tgv_set(self._h, level, ptr(u), ptr(v), ptr(w), ptr(p), step, t,
