@@ -70,6 +70,7 @@ struct sem_ctx {
     // host-pointer staging
     void *stage[2];
     size_t stage_bytes;
+    void *pipe;           // streams and events of the pipelined host-buffer sem_ax (lazy)
 };
 
 static inline int64_t sem_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -1,4 +1,6 @@
 // ops.cu -- stand-alone operator entry points: sem_ax, sem_dssum, sem_jacobi.
+#include <stdlib.h>
+
 #include "common.cuh"
 #include "gs.cuh"
 
@@ -75,30 +77,115 @@ int sem_ax_dev(sem_ctx *c, const void *u, void *w, double h1, double h2, sem_dty
     return SEM_ERR_ARG;
 }
 
+// ---------------------------------------------------------------------------
+// Host buffers: the operator in element chunks on three streams, so that the
+// copy of chunk k+1 to the device, the operator on chunk k and the copy of
+// chunk k-1 back to the host overlap (the host link carries both directions
+// at once).  A chunk is a contiguous element range; its geometry is the same
+// range of the element-blocked factors.
+// ---------------------------------------------------------------------------
+
+#define SEM_PIPE_CHUNKS 8
+
+struct AxPipe {
+    cudaStream_t in, out;
+    cudaEvent_t start, done, ev_in[SEM_PIPE_CHUNKS], ev_cmp[SEM_PIPE_CHUNKS];
+};
+
+void sem_pipe_destroy(void *pipe)
+{
+    AxPipe *P = (AxPipe *)pipe;
+    if (!P) return;
+    cudaStreamDestroy(P->in);
+    cudaStreamDestroy(P->out);
+    cudaEventDestroy(P->start);
+    cudaEventDestroy(P->done);
+    for (int k = 0; k < SEM_PIPE_CHUNKS; ++k) {
+        cudaEventDestroy(P->ev_in[k]);
+        cudaEventDestroy(P->ev_cmp[k]);
+    }
+    free(P);
+}
+
+static AxPipe *ax_pipe(sem_ctx *c)
+{
+    if (c->pipe) return (AxPipe *)c->pipe;
+    AxPipe *P = (AxPipe *)calloc(1, sizeof(AxPipe));
+    if (!P) return nullptr;
+    bool ok = cudaStreamCreateWithFlags(&P->in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&P->out, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&P->start, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&P->done, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < SEM_PIPE_CHUNKS; ++k)
+        ok = cudaEventCreateWithFlags(&P->ev_in[k], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&P->ev_cmp[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free(P);  // (handles created before the failure are left to the driver's teardown)
+        return nullptr;
+    }
+    c->pipe = P;
+    return P;
+}
+
+int sem_ensure_stage(sem_ctx *c, size_t bytes);  // setup.cu
+
+static int ax_host(sem_ctx *c, const void *u, void *w, bool uh, bool wh, double h1, double h2,
+                   sem_dtype dt, cudaStream_t s)
+{
+    const size_t es = (dt == SEM_F64 || dt == SEM_F64_NATIVE) ? sizeof(double) : sizeof(float);
+    const int64_t n3 = (int64_t)c->n * c->n * c->n;
+    int rc = sem_ensure_stage(c, (size_t)c->nL * es);
+    if (rc) return rc;
+    AxPipe *P = ax_pipe(c);
+    if (!P) return SEM_ERR_NOMEM;
+    const int K = c->E >= 2 * SEM_PIPE_CHUNKS ? SEM_PIPE_CHUNKS : 1;
+    const int64_t ne = sem_ceil_div(c->E, K);
+    char *ud = uh ? (char *)c->stage[0] : (char *)u;
+    char *wd = wh ? (char *)c->stage[1] : (char *)w;
+    SEM_CUDA(cudaEventRecord(P->start, s));
+    SEM_CUDA(cudaStreamWaitEvent(P->in, P->start, 0));
+    SEM_CUDA(cudaStreamWaitEvent(P->out, P->start, 0));
+    for (int k = 0; k < K; ++k) {
+        const int64_t e0 = k * ne, e1 = e0 + ne < c->E ? e0 + ne : c->E;
+        if (e0 >= e1) break;
+        const size_t off = (size_t)(e0 * n3) * es, bytes = (size_t)((e1 - e0) * n3) * es;
+        if (uh) {
+            SEM_CUDA(cudaMemcpyAsync(ud + off, (const char *)u + off, bytes, cudaMemcpyHostToDevice, P->in));
+            SEM_CUDA(cudaEventRecord(P->ev_in[k], P->in));
+            SEM_CUDA(cudaStreamWaitEvent(s, P->ev_in[k], 0));
+        }
+        sem_ctx sub = *c;  // the chunk's elements and their geometry
+        sub.E = e1 - e0;
+        sub.nL = (e1 - e0) * n3;
+        sub.geo64 = c->geo64 ? c->geo64 + e0 * 7 * n3 : nullptr;
+        sub.geo32 = c->geo32 ? c->geo32 + e0 * 7 * n3 : nullptr;
+        sub.geodf = c->geodf ? (void *)((char *)c->geodf + e0 * 7 * n3 * 8) : nullptr;
+        rc = sem_ax_dev(&sub, ud + off, wd + off, h1, h2, dt, s);
+        if (rc) return rc;
+        if (wh) {
+            SEM_CUDA(cudaEventRecord(P->ev_cmp[k], s));
+            SEM_CUDA(cudaStreamWaitEvent(P->out, P->ev_cmp[k], 0));
+            SEM_CUDA(cudaMemcpyAsync((char *)w + off, wd + off, bytes, cudaMemcpyDeviceToHost, P->out));
+        }
+    }
+    if (wh) {
+        SEM_CUDA(cudaEventRecord(P->done, P->out));
+        SEM_CUDA(cudaStreamWaitEvent(s, P->done, 0));
+    }
+    SEM_CUDA(cudaStreamSynchronize(s));
+    return SEM_OK;
+}
+
 extern "C" int sem_ax(sem_ctx *c, const void *u, void *w, double h1, double h2, sem_dtype dt,
                       void *stream)
 {
     if (!c || !u || !w) return SEM_ERR_ARG;
     if (dt < SEM_F64 || dt > SEM_F64_NATIVE) return SEM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool f64 = dt == SEM_F64 || dt == SEM_F64_NATIVE;
-    size_t bytes = (size_t)c->nL * (f64 ? sizeof(double) : sizeof(float));
-    const void *ud;
-    void *wd;
-    int uh, wh;
-    int rc = sem_stage_in(c, u, bytes, 0, s, &ud, &uh);
-    if (rc) return rc;
-    rc = sem_stage_out_ptr(c, w, bytes, 1, &wd, &wh);
-    if (rc) return rc;
-    rc = sem_ax_dev(c, ud, wd, h1, h2, dt, s);
-    if (rc) return rc;
-    if (wh) {
-        SEM_CUDA(cudaMemcpyAsync(w, wd, bytes, cudaMemcpyDeviceToHost, s));
-        SEM_CUDA(cudaStreamSynchronize(s));
-    } else if (uh) {
-        SEM_CUDA(cudaStreamSynchronize(s));
-    }
-    return SEM_OK;
+    const bool uh = !sem_is_device_ptr(u), wh = !sem_is_device_ptr(w);
+    if (uh || wh) return ax_host(c, u, w, uh, wh, h1, h2, dt, s);
+    return sem_ax_dev(c, u, w, h1, h2, dt, s);
 }
 
 // ---------------------------------------------------------------------------

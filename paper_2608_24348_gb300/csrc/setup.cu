@@ -292,10 +292,13 @@ static void free_ws(sem_ws &w)
     memset(&w, 0, sizeof(w));
 }
 
+void sem_pipe_destroy(void *pipe);  // ops.cu
+
 extern "C" void sem_destroy(sem_ctx *c)
 {
     if (!c) return;
     cudaDeviceSynchronize();
+    sem_pipe_destroy(c->pipe);
     void *ps[] = {c->tab64, c->tab32, c->geo64, c->geo32, c->geodf, c->tabdf, c->tabdfeo, c->vert, c->jinv64, c->jinv32, c->err_dev,
                   c->solve_dev, c->partials, c->stage[0], c->stage[1]};
     for (void *p : ps)
@@ -440,7 +443,7 @@ int sem_is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-static int ensure_stage(sem_ctx *c, size_t bytes)
+int sem_ensure_stage(sem_ctx *c, size_t bytes)
 {
     if (bytes <= c->stage_bytes) return SEM_OK;
     for (int k = 0; k < 2; ++k) {
@@ -462,7 +465,7 @@ int sem_stage_in(sem_ctx *c, const void *p, size_t bytes, int slot, cudaStream_t
         *is_host = 0;
         return SEM_OK;
     }
-    int rc = ensure_stage(c, bytes);
+    int rc = sem_ensure_stage(c, bytes);
     if (rc) return rc;
     SEM_CUDA(cudaMemcpyAsync(c->stage[slot], p, bytes, cudaMemcpyHostToDevice, s));
     *dev = c->stage[slot];
@@ -477,7 +480,7 @@ int sem_stage_out_ptr(sem_ctx *c, void *p, size_t bytes, int slot, void **dev, i
         *is_host = 0;
         return SEM_OK;
     }
-    int rc = ensure_stage(c, bytes);
+    int rc = sem_ensure_stage(c, bytes);
     if (rc) return rc;
     *dev = c->stage[slot];
     *is_host = 1;
