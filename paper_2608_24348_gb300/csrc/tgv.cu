@@ -30,6 +30,7 @@
 #include <cuda_fp16.h>
 
 #include "common.cuh"
+#include "df64.cuh"
 #include "gs.cuh"
 
 GsDesc sem_gs_desc(const sem_ctx *c);
@@ -80,6 +81,8 @@ struct sem_tgv {
     double *part;      // [E][2]
     double *tab64;     // eta[M], wq[M], J[M*n]
     float *tab32;
+    df64 *tabdf;       // the same tables as float pairs (FP64-accurate convection)
+    df64 *jinvdf;      // J^{-1} as float pairs, [E][9][n^3]
     TgvLogEntry *log;  // device ring
     TgvLogEntry *hlog; // pinned host copy
     TgvDev *dev;
@@ -599,6 +602,13 @@ __global__ void k_tgv_log_iters(const char *state, int stride, int iters_off, in
     }
 }
 
+// FP64 values as float pairs (hi = round(v), lo = round(v - hi)).
+__global__ void k_split_df64(const double *__restrict__ a, df64 *__restrict__ out, int64_t n)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) out[t] = df64(a[t]);
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -626,8 +636,8 @@ template <int NP>
 static int launch_convect(sem_tgv *T, const double *const u[3], double *const C[3], cudaStream_t s)
 {
     sem_ctx *c = T->c;
-    const bool f32 = T->op != SEM_F64;
-    const size_t smem = conv_smem<NP>(f32);
+    const bool f32 = T->op != SEM_F64 && T->op != SEM_F64_NATIVE;
+    const size_t smem = conv_smem<NP>(f32);  // (a float pair has the size of a double)
     if (smem > 227 * 1024) return SEM_ERR_ARG;
     ConvArgs a;
     for (int k = 0; k < 3; ++k) {
@@ -648,6 +658,12 @@ static int launch_convect(sem_tgv *T, const double *const u[3], double *const C[
         if (T->op == SEM_BF16_TC)
             return run_convect<NP, float, 2>(a, grid, smem, s);
         return run_convect<NP, float, 0>(a, grid, smem, s);
+    }
+    if (T->op == SEM_F64) {  // FP64-accurate on the FP32 pipes
+        a.jinv = T->jinvdf;
+        a.D = c->tabdf;
+        a.tab = T->tabdf;
+        return run_convect<NP, df64, 0>(a, grid, smem, s);
     }
     a.jinv = c->jinv64;
     a.D = c->tab64 + 2 * c->n;
@@ -817,6 +833,8 @@ extern "C" void sem_tgv_destroy(sem_tgv *T)
     if (T->part) cudaFree(T->part);
     if (T->tab64) cudaFree(T->tab64);
     if (T->tab32) cudaFree(T->tab32);
+    if (T->tabdf) cudaFree(T->tabdf);
+    if (T->jinvdf) cudaFree(T->jinvdf);
     if (T->log) cudaFree(T->log);
     if (T->dev) cudaFree(T->dev);
     if (T->hlog) cudaFreeHost(T->hlog);
@@ -828,7 +846,8 @@ extern "C" int sem_tgv_init(sem_ctx *c, double nu, double dt, sem_dtype op, cons
 {
     if (!out) return SEM_ERR_ARG;
     *out = nullptr;
-    if (!c || !(nu > 0) || !(dt > 0) || (op != SEM_F64 && op != SEM_F32)) return SEM_ERR_ARG;
+    if (!c || !(nu > 0) || !(dt > 0) || (op != SEM_F64 && op != SEM_F32 && op != SEM_F64_NATIVE))
+        return SEM_ERR_ARG;
     if (!c->periodic[0] || !c->periodic[1] || !c->periodic[2] || c->n > 10) return SEM_ERR_ARG;
     sem_tgv *T = (sem_tgv *)calloc(1, sizeof(sem_tgv));
     if (!T) return SEM_ERR_NOMEM;
@@ -886,6 +905,15 @@ extern "C" int sem_tgv_init(sem_ctx *c, double nu, double dt, sem_dtype op, cons
     TGV_TRY(cudaMalloc(&T->tab32, sizeof(float) * ntab));
     TGV_TRY(cudaMemcpy(T->tab64, h64, sizeof(double) * ntab, cudaMemcpyHostToDevice));
     TGV_TRY(cudaMemcpy(T->tab32, h32, sizeof(float) * ntab, cudaMemcpyHostToDevice));
+    {
+        df64 hdf[2 * 64 + 64 * SEM_NPMAX];
+        for (int t = 0; t < ntab; ++t) {
+            const float h = (float)h64[t];
+            hdf[t] = df64(h, (float)(h64[t] - (double)h));
+        }
+        TGV_TRY(cudaMalloc(&T->tabdf, sizeof(df64) * ntab));
+        TGV_TRY(cudaMemcpy(T->tabdf, hdf, sizeof(df64) * ntab, cudaMemcpyHostToDevice));
+    }
     TGV_TRY(cudaMalloc(&T->log, sizeof(TgvLogEntry) * TGV_LOG));
     TGV_TRY(cudaMemset(T->log, 0, sizeof(TgvLogEntry) * TGV_LOG));
     TGV_TRY(cudaMallocHost(&T->hlog, sizeof(TgvLogEntry) * TGV_LOG));
@@ -898,6 +926,9 @@ extern "C" int sem_tgv_init(sem_ctx *c, double nu, double dt, sem_dtype op, cons
         int rc = sem_run_geometry(c, nullptr, true, 0);
         if (rc) { sem_tgv_destroy(T); return rc; }
     }
+    TGV_TRY(cudaMalloc(&T->jinvdf, sizeof(df64) * 9 * nL));
+    k_split_df64<<<(unsigned)sem_ceil_div(9 * nL, 256), 256>>>(c->jinv64, T->jinvdf, 9 * nL);
+    TGV_TRY(cudaGetLastError());
     while (c->nws < 3) {
         int rc = sem_alloc_ws(c, c->nws);
         if (rc) { sem_tgv_destroy(T); return rc; }
@@ -1186,7 +1217,7 @@ extern "C" int sem_tgv_set_projection(sem_tgv *T, int max_vectors)
 
 static bool conv_dtype_ok(sem_dtype d)
 {
-    return d == SEM_F64 || d == SEM_F32 || d == SEM_F16_TC || d == SEM_BF16_TC;
+    return d == SEM_F64 || d == SEM_F64_NATIVE || d == SEM_F32 || d == SEM_F16_TC || d == SEM_BF16_TC;
 }
 
 static bool solve_dtype_ok(sem_dtype d)
