@@ -252,8 +252,9 @@ typedef struct {
 } sem_tgv_diag;
 
 /* Stepper on a periodic context (N <= 9).  nu: viscosity; dt: time step.
- * op: SEM_F64, or SEM_F32 = FP32 dealiased convection (histories, right-hand
- * sides, refinement residuals and diagnostics stay FP64).  vel / pres: options
+ * op: precision of the dealiased convection: SEM_F64 (FP64-accurate, float
+ * pairs on the FP32 pipes), SEM_F64_NATIVE (FP64 arithmetic) or SEM_F32
+ * (histories, right-hand sides, refinement residuals and diagnostics stay FP64).  vel / pres: options
  * of the velocity Helmholtz and pressure Poisson solves (NULL = defaults: FP64
  * PCG; with op = SEM_F32 the default pressure solve is an FP32 inner PCG inside
  * FP64 refinement).  The solves' inner field selects their precision. */
@@ -263,7 +264,8 @@ SEM_API int sem_tgv_init(sem_ctx *ctx, double nu, double dt, sem_dtype op, const
 /* Three-level precision policy of the stepper (Sec. 2, Fig. 2; the configurations
  * of Table 2).  One rule gives, per program block, the precision of each role:
  *  - sem: compute precision of the dealiased convection (the SEM block):
- *    SEM_F64, SEM_F32, or the kernel-level overrides SEM_F16_TC / SEM_BF16_TC =
+ *    SEM_F64 (FP64-accurate on the FP32 pipes), SEM_F64_NATIVE, SEM_F32, or the
+ *    kernel-level overrides SEM_F16_TC / SEM_BF16_TC =
  *    every operand of its contractions rounded to FP16 / BF16, FP32 accumulation;
  *  - vel, pres: compute precision of the three velocity Helmholtz solves and of
  *    the pressure Poisson solve: SEM_F64 (PCG on the FP64-accurate operator),
