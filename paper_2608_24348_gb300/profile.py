@@ -20,6 +20,7 @@ def main(argv=None):
     ap.add_argument("--N", type=int, default=7)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--maxit", type=int, default=20)
+    ap.add_argument("--projection", type=int, default=0, help="TGV: pressure projection space")
     args = ap.parse_args(argv)
 
     import json
@@ -58,6 +59,8 @@ def main(argv=None):
         x, y, z = xyz.view(3, -1)
         uu, vv, ww, pp = inputs.tgv_initial(x, y, z, lib=torch)
         T = sem.TGV(ctx, 1.0 / 1600, 1e-3, op=args.kernel[4:])
+        if args.projection:
+            T.set_projection(args.projection)
         T.set(uu.contiguous(), vv.contiguous(), (ww + 0 * x).contiguous(), pp.contiguous())
         T.step(3)  # startup orders 1, 2 and the first third-order step (graph capture)
         torch.cuda.synchronize()
