@@ -34,6 +34,9 @@ void sem_note_cuda_error(cudaError_t e, const char *where);
 struct sem_ws {
     double *r, *p, *w, *minv, *b;   // FP64 E-vectors (b: mean-free scratch copy is not kept)
     float *r32, *p32, *w32, *d32, *minv32;
+    // minv (and minv32) hold the Jacobi inverse of (jac_h1, jac_h2) when jac_ok (jac32_ok)
+    double jac_h1, jac_h2;
+    int jac_ok, jac32_ok;
 };
 
 struct sem_ctx {
@@ -58,8 +61,9 @@ struct sem_ctx {
     double *jinv64;    // [E][9][n^3] dr_a/dx_c at a*3+c (allocated by the stepper)
     float *jinv32;
     // solver workspaces (slot 0 allocated at setup)
-    int nws;
-    sem_ws ws[4];
+    int nws;              // (unused)
+    sem_ws ws[8];         // 0-3: solves through the API; 4-7: the Taylor-Green stepper's own
+                          // (allocated on first use; a slot is allocated when its r is set)
     // device-side solve state + pinned host mirror of the last solve's info
     void *solve_dev;      // sem_solve_state[1]
     void *solve_host;     // pinned

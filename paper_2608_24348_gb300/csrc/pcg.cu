@@ -55,7 +55,10 @@ static int ne_for(int n) { return (256 / (n * n)) > 0 ? 256 / (n * n) : 1; }
 // Element groups of the TC path use one warp per element.
 static int TcNE(int n) { return n <= 8 ? 8 : 4; }
 
-static void fill_desc(const sem_ctx *c, const sem_ws &ws, const double *b, double *x, double h1,
+// Fills d for a solve on workspace ws; the Jacobi inverse is recomputed unless
+// ws still holds the one of (h1, h2) (and its FP32 copy when mixed), and ws
+// records what the launch leaves in minv / minv32.
+static void fill_desc(const sem_ctx *c, sem_ws &ws, const double *b, double *x, double h1,
                       double h2, bool mixed, bool tc, ProbDesc &d)
 {
     memset(&d, 0, sizeof(d));
@@ -83,6 +86,13 @@ static void fill_desc(const sem_ctx *c, const sem_ws &ws, const double *b, doubl
     d.p = ws.p;
     d.w = ws.w;
     d.minv = ws.minv;
+    d.jac_cached = ws.jac_ok && ws.jac_h1 == h1 && ws.jac_h2 == h2 && (!mixed || ws.jac32_ok);
+    if (!d.jac_cached) {
+        ws.jac_ok = 1;
+        ws.jac_h1 = h1;
+        ws.jac_h2 = h2;
+        ws.jac32_ok = mixed;
+    }
     if (mixed) {
         d.r32 = ws.r32;
         d.p32 = ws.p32;
@@ -180,6 +190,15 @@ extern "C" int sem_last_solve_info(sem_ctx *c, sem_solve_info *info)
     return SEM_OK;
 }
 
+// A launch that failed to enqueue left the workspaces' Jacobi vectors as they
+// were: forget what fill_desc recorded for them.
+static int jac_forget(sem_ctx *c, int rc)
+{
+    if (rc != SEM_OK)
+        for (int k = 0; k < 8; ++k) c->ws[k].jac_ok = c->ws[k].jac32_ok = 0;
+    return rc;
+}
+
 // Device-pointer solve used by the stepper.
 int sem_pcg_solve_dev(sem_ctx *c, int slot, const double *b, double *x, double h1, double h2,
                       const sem_solve_opts &o, cudaStream_t s)
@@ -189,20 +208,22 @@ int sem_pcg_solve_dev(sem_ctx *c, int slot, const double *b, double *x, double h
     if (tc && c->n > 10) return SEM_ERR_ARG;
     ProbDesc d;
     fill_desc(c, c->ws[slot], b, x, h1, h2, mixed, tc, d);
-    return enqueue(c, o, &d, 1, s);
+    return jac_forget(c, enqueue(c, o, &d, 1, s));
 }
 
 // Several device-pointer solves on one context (workspace slots 0..np-1) in one launch.
 int sem_pcg_solve_dev_batch(sem_ctx *c, int np, const double *const *b, double *const *x, double h1,
-                            double h2, const sem_solve_opts &o, cudaStream_t s)
+                            double h2, const sem_solve_opts &o, cudaStream_t s, int slot0)
 {
-    if (np < 1 || np > 8 || np > c->nws) return SEM_ERR_ARG;
+    if (np < 1 || np > 4 || slot0 < 0 || slot0 + np > 8) return SEM_ERR_ARG;
+    for (int p = 0; p < np; ++p)
+        if (!c->ws[slot0 + p].r) return SEM_ERR_ARG;
     const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
     const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC;
     if (tc && c->n > 10) return SEM_ERR_ARG;
     ProbDesc d[8];
-    for (int p = 0; p < np; ++p) fill_desc(c, c->ws[p], b[p], x[p], h1, h2, mixed, tc, d[p]);
-    return enqueue(c, o, d, np, s);
+    for (int p = 0; p < np; ++p) fill_desc(c, c->ws[slot0 + p], b[p], x[p], h1, h2, mixed, tc, d[p]);
+    return jac_forget(c, enqueue(c, o, d, np, s));
 }
 
 // Device address of the solver state of problem p of the last launch (iters, status).
@@ -275,10 +296,9 @@ extern "C" int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const doub
         if (!sem_is_device_ptr(b[p]) || !sem_is_device_ptr(x[p])) return SEM_ERR_ARG;
         for (int q = 0; q < p; ++q) slot[p] += (ctxs[q] == c);
         if (slot[p] >= 4) return SEM_ERR_ARG;
-        while (c->nws <= slot[p]) {  // first use of a repeated context: one more workspace
-            rc = sem_alloc_ws(c, c->nws);
+        if (!c->ws[slot[p]].r) {  // first use of a repeated context: one more workspace
+            rc = sem_alloc_ws(c, slot[p]);
             if (rc) return rc;
-            c->nws += 1;
         }
         fill_desc(c, c->ws[slot[p]], b[p], x[p], h1[p], h2[p], mixed, tc, d[p]);
     }
@@ -290,7 +310,10 @@ extern "C" int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const doub
     }
     if ((same && nprob <= 8) || multi_ok) {
         rc = enqueue(owner, o, d.data(), nprob, s);
-        if (rc) return rc;
+        if (rc) {
+            for (int p = 0; p < nprob; ++p) jac_forget(ctxs[p], rc);
+            return rc;
+        }
         if (infos) {
             SEM_CUDA(cudaStreamSynchronize(s));
             int worst = SEM_OK;
@@ -306,7 +329,10 @@ extern "C" int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const doub
     int worst = SEM_OK;
     for (int p = 0; p < nprob; ++p) {
         rc = enqueue(owner, o, &d[p], 1, s);
-        if (rc) return rc;
+        if (rc) {
+            for (int q = 0; q < nprob; ++q) jac_forget(ctxs[q], rc);
+            return rc;
+        }
         if (infos) {
             SEM_CUDA(cudaStreamSynchronize(s));
             read_info(owner, 0, &infos[p]);

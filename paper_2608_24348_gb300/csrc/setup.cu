@@ -304,7 +304,7 @@ extern "C" void sem_destroy(sem_ctx *c)
     for (void *p : ps)
         if (p) cudaFree(p);
     if (c->solve_host) cudaFreeHost(c->solve_host);
-    for (int s = 0; s < c->nws; ++s) free_ws(c->ws[s]);
+    for (int s = 0; s < 8; ++s) free_ws(c->ws[s]);
     free(c);
 }
 

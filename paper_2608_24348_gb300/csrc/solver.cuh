@@ -75,6 +75,7 @@ enum SolvePhase {
 
 struct ProbDesc {
     int n, NE, NE32, singular;  // NE: elements per group (CUDA cores); NE32: inner operator
+    int jac_cached;             // minv (and minv32 if mixed) already hold this problem's Jacobi inverse
     int64_t E, nL, nG;
     GsDesc gs;
     double volume, h1, h2;
@@ -561,6 +562,12 @@ __device__ __forceinline__ void uniq_item(const ProbDesc &P, const PState &S, in
     }
     switch (ph) {
         case PH_JACGS: {
+            if (P.jac_cached) {  // the Jacobi inverse is kept from an earlier solve: only sum b
+#pragma unroll
+                for (int r = 0; r < RU; ++r)
+                    if (ok[r]) v[0] += __ldcg(P.b + R[r].off[0] + xo[0]);
+                break;
+            }
             double s[RU], bv[RU];
 #pragma unroll
             for (int r = 0; r < RU; ++r) {
@@ -864,7 +871,7 @@ __global__ void __launch_bounds__(SEM_SOLVE_THREADS, MODE == MODE_F32 ? SEM_SOLV
             for (int p = 0; p < np; ++p) {
                 int ph;
                 if (step == 0) {
-                    ph = PH_JAC;
+                    ph = prm.prob[p].jac_cached ? PH_JACGS : PH_JAC;
                 } else {
                     ph = ((volatile int *)prm.sched)[p];
                 }

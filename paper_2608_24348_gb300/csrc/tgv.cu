@@ -41,7 +41,7 @@ int sem_ax_dev(sem_ctx *c, const void *u, void *w, double h1, double h2, sem_dty
 int sem_pcg_solve_dev(sem_ctx *c, int slot, const double *b, double *x, double h1, double h2,
                       const sem_solve_opts &o, cudaStream_t s);
 int sem_pcg_solve_dev_batch(sem_ctx *c, int np, const double *const *b, double *const *x, double h1,
-                            double h2, const sem_solve_opts &o, cudaStream_t s);
+                            double h2, const sem_solve_opts &o, cudaStream_t s, int slot0);
 const void *sem_solve_state_ptr(const sem_ctx *c, int p, int *iters_off, int *status_off);
 const void *sem_solve_sync_ptr(const sem_ctx *c);
 
@@ -89,6 +89,7 @@ struct sem_tgv {
     cudaGraphExec_t graph;
     cudaStream_t graph_stream;
     int graph_state;   // 0 not tried, 1 ready, -1 unavailable
+    int graph_warm;    // a steady step ran directly since the last (re)capture was needed
     double *block;     // one allocation for all fields
 };
 
@@ -773,7 +774,7 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     SEM_CHECK_LAUNCH();
     rc = sem_dssum_dev(c, T->bp, SEM_F64, s);
     if (rc) return rc;
-    rc = T->proj_max > 0 ? pressure_projected(T, s) : sem_pcg_solve_dev(c, 0, T->bp, T->p, 1.0, 0.0, T->po, s);
+    rc = T->proj_max > 0 ? pressure_projected(T, s) : sem_pcg_solve_dev(c, 4, T->bp, T->p, 1.0, 0.0, T->po, s);
     if (rc) return rc;
     rc = round_stored(T, T->p, nL, s);
     if (rc) return rc;
@@ -806,7 +807,8 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     }
     const double *bb[3] = {T->rhs[0], T->rhs[1], T->rhs[2]};
     double *xx[3] = {T->unew[0], T->unew[1], T->unew[2]};
-    rc = sem_pcg_solve_dev_batch(c, 3, bb, xx, T->nu, k.b0 / T->dt, T->vo, s);
+    // (workspace slots 5-7; slot 4 keeps the pressure's Jacobi inverse between steps)
+    rc = sem_pcg_solve_dev_batch(c, 3, bb, xx, T->nu, k.b0 / T->dt, T->vo, s, 5);
     if (rc) return rc;
     k_tgv_log_iters<<<1, 32, 0, s>>>(st0, stride, io, so, serr, 1, 3, T->dev, T->log, 0);
     SEM_CHECK_LAUNCH();
@@ -929,10 +931,10 @@ extern "C" int sem_tgv_init(sem_ctx *c, double nu, double dt, sem_dtype op, cons
     TGV_TRY(cudaMalloc(&T->jinvdf, sizeof(df64) * 9 * nL));
     k_split_df64<<<(unsigned)sem_ceil_div(9 * nL, 256), 256>>>(c->jinv64, T->jinvdf, 9 * nL);
     TGV_TRY(cudaGetLastError());
-    while (c->nws < 3) {
-        int rc = sem_alloc_ws(c, c->nws);
+    for (int slot = 4; slot < 8; ++slot) {  // the stepper's own solver workspaces
+        if (c->ws[slot].r) continue;
+        int rc = sem_alloc_ws(c, slot);
         if (rc) { sem_tgv_destroy(T); return rc; }
-        c->nws += 1;
     }
     TGV_TRY(cudaDeviceSynchronize());
 #undef TGV_TRY
@@ -994,35 +996,43 @@ extern "C" int sem_tgv_set(sem_tgv *T, int level, const double *u, const double 
 #define TGV_PMAX 32   // largest basis
 #define TGV_PBLK 304  // blocks of the dot kernels (fixed: deterministic sums)
 
-// part[b][k] = block b's share of sum_i X_k[i] v[i] w[i], k < L (L = *Ld).
+// part[b][k] = block b's share of sum_i X_k[i] v[i] w[i], k < L (L = *Ld): the
+// basis is swept in chunks of TGV_PCH vectors, each with its accumulators in
+// registers (v and w are read once per chunk).
+#define TGV_PCH 8
 __global__ void __launch_bounds__(256, 2) k_proj_dot(const double *__restrict__ X, const double *__restrict__ v,
-                                                  const double *__restrict__ w, const int *__restrict__ Ld,
-                                                  int64_t n, double *__restrict__ part)
+                                                     const double *__restrict__ w, const int *__restrict__ Ld,
+                                                     int64_t n, double *__restrict__ part)
 {
-    __shared__ double red[8][TGV_PMAX];
+    __shared__ double red[8][TGV_PCH];
     const int L = *Ld;
-    double acc[TGV_PMAX];
-#pragma unroll
-    for (int k = 0; k < TGV_PMAX; ++k) acc[k] = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double t = v[i] * w[i];
-#pragma unroll
-        for (int k = 0; k < TGV_PMAX; ++k)
-            if (k < L) acc[k] = fma(__ldcg(X + (int64_t)k * n + i), t, acc[k]);
-    }
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int k0 = 0; k0 < L; k0 += TGV_PCH) {
+        const int m = L - k0 < TGV_PCH ? L - k0 : TGV_PCH;
+        double acc[TGV_PCH];
 #pragma unroll
-    for (int k = 0; k < TGV_PMAX; ++k) {
-        if (k >= L) break;
-        double a = acc[k];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) red[wp][k] = a;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < L; k += blockDim.x) {
-        double a = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += red[q][k];
-        part[(int64_t)blockIdx.x * TGV_PMAX + k] = a;
+        for (int k = 0; k < TGV_PCH; ++k) acc[k] = 0.0;
+        const double *Xc = X + (int64_t)k0 * n;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const double t = v[i] * w[i];
+#pragma unroll
+            for (int k = 0; k < TGV_PCH; ++k)
+                if (k < m) acc[k] = fma(__ldcg(Xc + (int64_t)k * n + i), t, acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < TGV_PCH; ++k) {
+            double a = acc[k];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) red[wp][k] = a;
+        }
+        __syncthreads();
+        if (threadIdx.x < m) {
+            double a = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += red[q][threadIdx.x];
+            part[(int64_t)blockIdx.x * TGV_PMAX + k0 + threadIdx.x] = a;
+        }
+        __syncthreads();
     }
 }
 
@@ -1149,7 +1159,7 @@ static int pressure_projected(sem_tgv *T, cudaStream_t s)
     SEM_CHECK_LAUNCH();
     // the remainder, from a zero guess
     SEM_CUDA(cudaMemsetAsync(T->pdx, 0, sizeof(double) * n, s));
-    if ((rc = sem_pcg_solve_dev(c, 0, T->pbq, T->pdx, 1.0, 0.0, T->po, s))) return rc;
+    if ((rc = sem_pcg_solve_dev(c, 4, T->pbq, T->pdx, 1.0, 0.0, T->po, s))) return rc;
     k_vec_add<<<g, 256, 0, s>>>(T->p, T->pxb, T->pdx, n);
     SEM_CHECK_LAUNCH();
     // basis update: v = dx (or p after a restart), A v, CGS twice, A-normalise, append
@@ -1183,6 +1193,7 @@ extern "C" int sem_tgv_set_projection(sem_tgv *T, int max_vectors)
     if (T->graph_state == 1) {
         cudaGraphExecDestroy(T->graph);
         T->graph_state = 0;
+        T->graph_warm = 0;
     }
     if (max_vectors == 0) return SEM_OK;
     sem_ctx *c = T->c;
@@ -1264,6 +1275,7 @@ static void apply_policy(sem_tgv *T, int step)
         cudaGraphExecDestroy(T->graph);
         T->graph_state = 0;
     }
+    T->graph_warm = 0;
     T->cur_rule = r;
 }
 
@@ -1279,7 +1291,12 @@ extern "C" int sem_tgv_step(sem_tgv *T, int nsteps, sem_tgv_diag *out, void *str
         const int q = T->step + 1 < 3 ? T->step + 1 : 3;
         int rc;
         apply_policy(T, T->step + 1);
-        if (q == 3 && s != 0 && T->graph_state == 0) {
+        if (q == 3 && s != 0 && T->graph_state == 0 && !T->graph_warm) {
+            // one steady step runs directly first, so the Jacobi inverses of its
+            // solves are cached when the next one is captured (the graph then
+            // keeps reusing them)
+            T->graph_warm = 1;
+        } else if (q == 3 && s != 0 && T->graph_state == 0) {
             // capture one steady-state step; fall back to direct launches if capture fails
             cudaGraph_t g = nullptr;
             T->graph_state = -1;
