@@ -169,7 +169,7 @@ struct ConvCfg {
     template <typename T>
     static constexpr size_t smem()
     {
-        return sizeof(T) * (size_t)(3 * N3 + 3 * N3 + 3 * M3 + M3 + T1 + T2 + M * NP + NP * NP + M + M + 32);
+        return sizeof(T) * (size_t)(3 * N3 + 3 * N3 + 3 * M3 + M3 + T1 + T2 + 2 * (M * NP + NP * NP) + M + M + 32);
     }
 };
 
@@ -196,9 +196,11 @@ __device__ __forceinline__ T rnd16(T x)
         return x;
 }
 
-// v = (J x J x J) in  (n^3 -> M^3); fin(q, value) receives each output.
+// v = (J x J x J) in  (n^3 -> M^3); fin(q, value) receives each output.  sJT is
+// J transposed ([l][q]): the first stage's 32 lanes then read consecutive words
+// (J row-major would put 12 rows 8 words apart on the same banks).
 template <int NP, typename T, int R16, class Fin>
-__device__ __forceinline__ void interp_fwd(const T *in, T *st1, T *st2, const T *sJ, Fin fin)
+__device__ __forceinline__ void interp_fwd(const T *in, T *st1, T *st2, const T *sJ, const T *sJT, Fin fin)
 {
     using C = ConvCfg<NP>;
     constexpr int M = C::M;
@@ -206,7 +208,7 @@ __device__ __forceinline__ void interp_fwd(const T *in, T *st1, T *st2, const T 
         const int q1 = t % M, j = (t / M) % NP, k = t / (M * NP);
         T s = 0;
 #pragma unroll
-        for (int l = 0; l < NP; ++l) s = fma(sJ[q1 * NP + l], in[(k * NP + j) * NP + l], s);
+        for (int l = 0; l < NP; ++l) s = fma(sJT[l * M + q1], in[(k * NP + j) * NP + l], s);
         st1[t] = rnd16<R16>(s);
     }
     __syncthreads();
@@ -273,13 +275,19 @@ __global__ void __launch_bounds__(256) k_convect(ConvArgs a)
     T *st1 = sf + M3, *st2 = st1 + C::T1;
     T *sJ = st2 + C::T2, *sD = sJ + M * NP, *seta = sD + NP * NP, *sw = seta + M;
     T *sc = sw + M;                       // trilinear coefficients [8][3]
+    T *sJT = sc + 32, *sDT = sJT + M * NP;  // J and D transposed (conflict-free lane patterns)
     const T *D = (const T *)a.D, *tab = (const T *)a.tab;
     for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sD[t] = rnd16<R16>(D[t]);
     for (int t = threadIdx.x; t < M; t += blockDim.x) {
         seta[t] = tab[t];
         sw[t] = tab[M + t];
     }
-    for (int t = threadIdx.x; t < M * NP; t += blockDim.x) sJ[t] = rnd16<R16>(tab[2 * M + t]);
+    for (int t = threadIdx.x; t < M * NP; t += blockDim.x) {
+        const T v = rnd16<R16>(tab[2 * M + t]);
+        sJ[t] = v;
+        sJT[(t % NP) * M + t / NP] = v;
+    }
+    for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sDT[(t % NP) * NP + t / NP] = rnd16<R16>(D[t]);
     const T *jinv = (const T *)a.jinv;
     for (int64_t e = blockIdx.x; e < a.E; e += gridDim.x) {
         __syncthreads();
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(256) k_convect(ConvArgs a)
         __syncthreads();
         // fine-grid velocity, scaled by the quadrature weight and |J|
         for (int d = 0; d < 3; ++d)
-            interp_fwd<NP, T, R16>(su + d * N3, st1, st2, sJ, [&](int q, T v) { sfu[d * M3 + q] = v; });
+            interp_fwd<NP, T, R16>(su + d * N3, st1, st2, sJ, sJT, [&](int q, T v) { sfu[d * M3 + q] = v; });
         for (int q = threadIdx.x; q < M3; q += blockDim.x) {
             const int q1 = q % M, q2 = (q / M) % M, q3 = q / (M * M);
             const T r = seta[q1], s = seta[q2], t = seta[q3];
@@ -332,7 +340,7 @@ __global__ void __launch_bounds__(256) k_convect(ConvArgs a)
                 T gr = 0, gs = 0, gt = 0;
 #pragma unroll
                 for (int l = 0; l < NP; ++l) {
-                    gr = fma(sD[i * NP + l], uc[(k * NP + j) * NP + l], gr);
+                    gr = fma(sDT[l * NP + i], uc[(k * NP + j) * NP + l], gr);
                     gs = fma(sD[j * NP + l], uc[(k * NP + l) * NP + i], gs);
                     gt = fma(sD[k * NP + l], uc[(l * NP + j) * NP + i], gt);
                 }
@@ -349,7 +357,7 @@ __global__ void __launch_bounds__(256) k_convect(ConvArgs a)
             for (int q = threadIdx.x; q < M3; q += blockDim.x) sf[q] = 0;
             __syncthreads();
             for (int d = 0; d < 3; ++d)
-                interp_fwd<NP, T, R16>(sg + d * N3, st1, st2, sJ,
+                interp_fwd<NP, T, R16>(sg + d * N3, st1, st2, sJ, sJT,
                                   [&](int q, T v) { sf[q] = fma(sfu[d * M3 + q], rnd16<R16>(v), sf[q]); });
             if (R16) {
                 __syncthreads();
@@ -414,22 +422,23 @@ __global__ void k_tgv_g(GArgs a)
 }
 
 // bp = sum_a D_a^T ( B sum_c (dr_a/dx_c) g_c )   (local, one block per element)
-template <int NP>
+// T = double, or df64 (FP64-accurate on the FP32 pipes): jinv, geo and D are
+// then the float-pair copies; g and bp stay FP64.
+template <int NP, typename T>
 __global__ void k_tgv_divg(const double *g0, const double *g1, const double *g2,
-                           const double *jinv, const double *geo64, const double *D, double *bp,
-                           int64_t E)
+                           const T *jinv, const T *geo, const T *D, double *bp, int64_t E)
 {
     constexpr int N3 = NP * NP * NP;
-    __shared__ double sh[3 * N3];
-    __shared__ double sD[NP * NP];
+    __shared__ T sh[3 * N3];
+    __shared__ T sD[NP * NP];
     for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sD[t] = D[t];
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         __syncthreads();
         const int64_t off = e * N3;
         for (int pn = threadIdx.x; pn < N3; pn += blockDim.x) {
-            const double gv[3] = {g0[off + pn], g1[off + pn], g2[off + pn]};
-            const double bm = geo64[(e * 7 + 6) * N3 + pn];
-            const double *ji = jinv + e * 9 * N3 + pn;
+            const T gv[3] = {T(g0[off + pn]), T(g1[off + pn]), T(g2[off + pn])};
+            const T bm = geo[(e * 7 + 6) * N3 + pn];
+            const T *ji = jinv + e * 9 * N3 + pn;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
                 sh[a * N3 + pn] = bm * (ji[(a * 3 + 0) * N3] * gv[0] + ji[(a * 3 + 1) * N3] * gv[1] +
@@ -438,14 +447,14 @@ __global__ void k_tgv_divg(const double *g0, const double *g1, const double *g2,
         __syncthreads();
         for (int pn = threadIdx.x; pn < N3; pn += blockDim.x) {
             const int i = pn % NP, j = (pn / NP) % NP, k = pn / (NP * NP);
-            double s = 0.0;
+            T s = 0;
 #pragma unroll
             for (int l = 0; l < NP; ++l) {
-                s += sD[l * NP + i] * sh[0 * N3 + (k * NP + j) * NP + l];
-                s += sD[l * NP + j] * sh[1 * N3 + (k * NP + l) * NP + i];
-                s += sD[l * NP + k] * sh[2 * N3 + (l * NP + j) * NP + i];
+                s = fma(sD[l * NP + i], sh[0 * N3 + (k * NP + j) * NP + l], s);
+                s = fma(sD[l * NP + j], sh[1 * N3 + (k * NP + l) * NP + i], s);
+                s = fma(sD[l * NP + k], sh[2 * N3 + (l * NP + j) * NP + i], s);
             }
-            bp[off + pn] = s;
+            bp[off + pn] = (double)s;
         }
     }
 }
@@ -498,44 +507,48 @@ __global__ void k_tgv_vrhs(VArgs a)
 }
 
 // Per-element sum of B|u|^2 and B|curl u|^2.
-template <int NP>
+// T as in k_tgv_divg: the gradients, the vorticity and both integrals per
+// element in T; the block sums in FP64.
+template <int NP, typename T>
 __global__ void k_tgv_diag_part(const double *u0, const double *u1, const double *u2,
-                                const double *jinv, const double *geo64, const double *D,
-                                double *part, int64_t E)
+                                const T *jinv, const T *geo, const T *D, double *part, int64_t E)
 {
     constexpr int N3 = NP * NP * NP;
-    __shared__ double su[3 * N3];
-    __shared__ double sD[NP * NP];
+    __shared__ T su[3 * N3];
+    __shared__ T sD[NP * NP];
     __shared__ double sred[2 * 32];
     for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sD[t] = D[t];
     const double *uu[3] = {u0, u1, u2};
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         __syncthreads();
         const int64_t off = e * N3;
-        for (int t = threadIdx.x; t < 3 * N3; t += blockDim.x) su[t] = uu[t / N3][off + t % N3];
+        for (int t = threadIdx.x; t < 3 * N3; t += blockDim.x) su[t] = T(uu[t / N3][off + t % N3]);
         __syncthreads();
-        double ke = 0.0, en = 0.0;
+        T tke = 0, ten = 0;
         for (int pn = threadIdx.x; pn < N3; pn += blockDim.x) {
             const int i = pn % NP, j = (pn / NP) % NP, k = pn / (NP * NP);
-            const double *ji = jinv + e * 9 * N3 + pn;
-            double du[3][3];  // du[c][d] = du_c / dx_d
+            const T *ji = jinv + e * 9 * N3 + pn;
+            T du[3][3];  // du[c][d] = du_c / dx_d
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const double *uc = su + c * N3;
-                double gr = 0, gs = 0, gt = 0;
+                const T *uc = su + c * N3;
+                T gr = 0, gs = 0, gt = 0;
 #pragma unroll
                 for (int l = 0; l < NP; ++l) {
-                    gr += sD[i * NP + l] * uc[(k * NP + j) * NP + l];
-                    gs += sD[j * NP + l] * uc[(k * NP + l) * NP + i];
-                    gt += sD[k * NP + l] * uc[(l * NP + j) * NP + i];
+                    gr = fma(sD[i * NP + l], uc[(k * NP + j) * NP + l], gr);
+                    gs = fma(sD[j * NP + l], uc[(k * NP + l) * NP + i], gs);
+                    gt = fma(sD[k * NP + l], uc[(l * NP + j) * NP + i], gt);
                 }
+#pragma unroll
                 for (int d = 0; d < 3; ++d)
-                    du[c][d] = ji[(0 * 3 + d) * N3] * gr + ji[(1 * 3 + d) * N3] * gs + ji[(2 * 3 + d) * N3] * gt;
+                    du[c][d] = fma(ji[(0 * 3 + d) * N3], gr, fma(ji[(1 * 3 + d) * N3], gs, ji[(2 * 3 + d) * N3] * gt));
             }
-            const double wx = du[2][1] - du[1][2], wy = du[0][2] - du[2][0], wz = du[1][0] - du[0][1];
-            const double bm = geo64[(e * 7 + 6) * N3 + pn];
-            ke += bm * (su[pn] * su[pn] + su[N3 + pn] * su[N3 + pn] + su[2 * N3 + pn] * su[2 * N3 + pn]);
-            en += bm * (wx * wx + wy * wy + wz * wz);
+            const T wx = du[2][1] - du[1][2], wy = du[0][2] - du[2][0], wz = du[1][0] - du[0][1];
+            const T bm = geo[(e * 7 + 6) * N3 + pn];
+            tke = fma(bm, fma(su[pn], su[pn], fma(su[N3 + pn], su[N3 + pn], su[2 * N3 + pn] * su[2 * N3 + pn])), tke);
+            ten = fma(bm, fma(wx, wx, fma(wy, wy, wz * wz)), ten);
         }
+        double ke = (double)tke, en = (double)ten;
         for (int o = 16; o > 0; o >>= 1) {
             ke += __shfl_xor_sync(0xffffffffu, ke, o);
             en += __shfl_xor_sync(0xffffffffu, en, o);
@@ -724,9 +737,10 @@ static int diag(sem_tgv *T, int advance, cudaStream_t s)
 {
     sem_ctx *c = T->c;
     const int blocks = (int)(c->E < 65535 * 16 ? c->E : 65535 * 16);
-    TGV_DISPATCH(c->n, k_tgv_diag_part<NP><<<blocks, 256, 0, s>>>(T->u[0][0], T->u[0][1], T->u[0][2],
-                                                                c->jinv64, c->geo64, c->tab64 + 2 * c->n,
-                                                                T->part, c->E));
+    // FP64-accurate on the FP32 pipes (J^-1, B and D as float pairs)
+    TGV_DISPATCH(c->n, k_tgv_diag_part<NP, df64><<<blocks, 256, 0, s>>>(
+                           T->u[0][0], T->u[0][1], T->u[0][2], T->jinvdf, (const df64 *)c->geodf,
+                           (const df64 *)c->tabdf, T->part, c->E));
     SEM_CHECK_LAUNCH();
     const double V = c->volume;
     k_tgv_diag_final<<<1, 256, 0, s>>>(T->part, c->E, V, T->dt, T->dev, T->log, advance);
@@ -769,8 +783,9 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     SEM_CHECK_LAUNCH();
     // 4. pressure: weak divergence, dssum, Poisson solve from p^n
     const int blocks = (int)(c->E < 65535 * 16 ? c->E : 65535 * 16);
-    TGV_DISPATCH(c->n, k_tgv_divg<NP><<<blocks, 256, 0, s>>>(T->g[0], T->g[1], T->g[2], c->jinv64,
-                                                             c->geo64, c->tab64 + 2 * c->n, T->bp, c->E));
+    TGV_DISPATCH(c->n, k_tgv_divg<NP, df64><<<blocks, 256, 0, s>>>(T->g[0], T->g[1], T->g[2], T->jinvdf,
+                                                                   (const df64 *)c->geodf,
+                                                                   (const df64 *)c->tabdf, T->bp, c->E));
     SEM_CHECK_LAUNCH();
     rc = sem_dssum_dev(c, T->bp, SEM_F64, s);
     if (rc) return rc;
