@@ -86,6 +86,7 @@ def lib():
                                       ctypes.c_int, ctypes.c_double]
             L.orc_tgv_get.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
             L.orc_tgv_step.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
+            L.orc_tgv_set_storage.argtypes = [ctypes.c_void_p, ctypes.c_int]
             _lib = L
     return _lib
 
@@ -292,6 +293,10 @@ class TGV:
         out = np.zeros((4, self.nL))
         lib().orc_tgv_get(self._h, _p(out[0]), _p(out[1]), _p(out[2]), _p(out[3]))
         return out
+
+    def set_storage(self, store32):
+        """store32: keep the stored state as FP32 values (rp = fp32, Table 2 group B)."""
+        lib().orc_tgv_set_storage(self._h, int(bool(store32)))
 
     def step(self, nsteps=1):
         """Advance; returns diag rows {t, KE, enstrophy, it_p, it_u, it_v, it_w, status}."""

@@ -808,6 +808,7 @@ typedef struct {
     double tol_v, tol_p;
     int abs_tol, maxit;
     int step;                       /* steps taken so far */
+    int store32;                    /* stored state kept as FP32 values (rp = fp32, Table 2 group B) */
     double *vert, *D, *jinv, *G, *B, *Bsum;
     double *u[3][3];                /* u[h][c]: h = 0 -> u^n, 1 -> u^{n-1}, 2 -> u^{n-2} */
     double *C[3][3];                /* C[h][c]: convective term at the same levels */
@@ -872,6 +873,22 @@ void orc_tgv_destroy(void *h)
         for (int c = 0; c < 3; ++c) { free(s->u[a][c]); free(s->C[a][c]); }
     free(s->p); free(s->work); free(s->vert); free(s->D); free(s->jinv); free(s->G); free(s->B);
     free(s->Bsum); free(s);
+}
+
+/* Storage precision of the stepper's state (Sec. 4: the global precision rp
+ * is the storage format).  store32 != 0: the convective term, the pressure and
+ * the new velocity are rounded to FP32 values where each step stores them
+ * (the arithmetic stays FP64). */
+int orc_tgv_set_storage(void *hnd, int store32)
+{
+    orc_tgv *s = hnd;
+    s->store32 = store32 != 0;
+    return ORC_OK;
+}
+
+static void round_to_float(double *a, size_t n)
+{
+    for (size_t i = 0; i < n; ++i) a[i] = (double)(float)a[i];
 }
 
 /* Set u^{n-h} (h = 0,1,2) and, for h == 0, p^n; the convective history at
@@ -939,6 +956,8 @@ int orc_tgv_step(void *hnd, int nsteps, double *diag)
         /* 1. convective term at level n (C[0] holds it after the previous step's shift) */
         orc_convect(N, s->nelx, s->nely, s->nelz, s->vert, s->jinv, s->u[0][0], s->u[0][1],
                     s->u[0][2], s->C[0][0], s->C[0][1], s->C[0][2]);
+        if (s->store32)
+            for (int c = 0; c < 3; ++c) round_to_float(s->C[0][c], nL);
         /* 2-3. */
         for (int c = 0; c < 3; ++c) {
             for (size_t p = 0; p < nL; ++p)
@@ -975,6 +994,7 @@ int orc_tgv_step(void *hnd, int nsteps, double *diag)
                          s->p, s->tol_p, s->abs_tol, s->maxit, info);
         int itp = (int)info[0];
         if (rc != ORC_OK) rc_all = rc;
+        if (s->store32) round_to_float(s->p, nL);
         /* 5. pressure gradient (element-local) and velocity solves */
 #pragma omp parallel
         {
@@ -1016,6 +1036,7 @@ int orc_tgv_step(void *hnd, int nsteps, double *diag)
             s->C[2][c] = s->C[1][c];
             s->C[1][c] = s->C[0][c];
             s->C[0][c] = cn; /* overwritten by the next step's convective evaluation */
+            if (s->store32) round_to_float(s->u[0][c], nL);
         }
         s->step += 1;
         s->t += dt;

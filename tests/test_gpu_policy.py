@@ -101,3 +101,34 @@ def test_malformed_schedules_are_refused(sem, setup):
     with pytest.raises(sem.SemError):
         T.set_policy([policy.rule("A-0")] * 9)  # more than SEM_TGV_MAX_RULES
     T.close()
+
+
+def test_fp32_storage_matches_the_oracle_with_fp32_storage(sem):
+    """B-1 (FP64 compute, rp = fp32 storage) against the oracle run with the same
+    FP32 rounding of the stored state: the histories agree to FP64 round-off,
+    while the FP64-storage oracle differs by the FP32 rounding of the state."""
+    torch, _ = torch_dev()
+    n, nel, steps = 5, (3, 3, 3), 6
+    ctx, m, v = pair(sem, n, nel, 0.0)
+    T = sem.TGV(ctx, NU, DT, op="f64", vel=sem.opts(tol=1e-12), pres=sem.opts(tol=1e-12))
+    T.set_policy([policy.rule("B-1")])
+    x, y, z = gpu_coords(ctx)
+    u, vv, w, p = inputs.tgv_initial(x, y, z, lib=torch)
+    T.set(u.contiguous(), vv.contiguous(), (w + 0 * x).contiguous(), p.contiguous())
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        d = T.step(steps, stream=stream)
+    T.close()
+    assert all(r["status"] == 0 for r in d)
+    xo, yo, zo = m.xyz
+    ref = {}
+    for store32 in (True, False):
+        O = oracle.TGV(n, nel, v, (TWO_PI,) * 3, NU, DT, tol_v=1e-12, tol_p=1e-12, abs_tol=False)
+        O.set_storage(store32)
+        O.set(*inputs.tgv_initial(xo, yo, zo))
+        ref[store32] = O.step(steps)
+    for col, key in ((1, "ke"), (2, "enstrophy")):
+        h = [r[key] for r in d]
+        e32 = policy.e_max(h, ref[True][:, col])
+        e64 = policy.e_max(h, ref[False][:, col])
+        assert e32 <= 2e-11 and e64 >= 5e-10, (key, e32, e64)

@@ -442,3 +442,26 @@ def test_tgv_energy_balance():
     t = d[:, 0]
     slope = (d[-1, 1] - ke0) / t[-1]
     assert abs(slope - (-2 * nu * en0)) < 0.02 * 2 * nu * en0, (slope, -2 * nu * en0)
+
+
+def test_tgv_fp32_storage_mode():
+    """rp = fp32 (Table 2 group B): every stored value is an FP32 number; the
+    KE history moves by about the FP32 rounding of the state, no more."""
+    N, nel, nu, dt = 5, (3, 3, 3), 1.0 / 1600, 1e-3
+    v = inputs.box_vertices(nel, (2 * math.pi,) * 3)
+    m = oracle.Mesh(N, nel, v)
+    x, y, z = m.xyz
+    runs = []
+    for store32 in (False, True):
+        tgv = oracle.TGV(N, nel, v, (2 * math.pi,) * 3, nu, dt, tol_v=1e-12, tol_p=1e-12,
+                         abs_tol=False)
+        tgv.set_storage(store32)
+        tgv.set(*inputs.tgv_initial(x, y, z))
+        d = tgv.step(4)
+        assert np.all(d[:, 7] == 0)
+        runs.append((d, tgv.get()))
+    (d64, s64), (d32, s32) = runs
+    assert np.array_equal(s32, s32.astype(np.float32).astype(np.float64))
+    assert not np.array_equal(s64, s64.astype(np.float32).astype(np.float64))
+    rel = np.abs(d32[:, 1] - d64[:, 1]).max() / np.abs(d64[:, 1]).max()
+    assert 0.0 < rel < 1e-6, rel
