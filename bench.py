@@ -110,13 +110,20 @@ def dist_env():
 
 
 def barrier_max(x, ws):
+    """The largest x over the ws ranks (every rank gets it)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_gdofs(nodes_per_rank, seconds_max, ws):
+    """Whole-job throughput: every rank's replica, over the slowest rank's time."""
+    return ws * nodes_per_rank / seconds_max / 1e9
 
 
 def cpu_baseline(seconds=12.0):
@@ -288,7 +295,7 @@ def main():
 
     tot64 = barrier_max(tot64, ws)
     ms64 = tot64 / args.steps
-    gdof = lambda ms: ws * nL / (ms * 1e-3) / 1e9
+    gdof = lambda ms: aggregate_gdofs(nL, ms * 1e-3, ws)
     avg64 = statistics.mean(per64)
     mhz = clk.get("sm_max_mhz") or pk["sm_max_mhz"]
     fp32_peak = 128 * n_sms * mhz * 1e6 / 1e12          # FP32-pipe ops/s (T)
