@@ -131,14 +131,6 @@ __device__ __forceinline__ dfp df_sum(dfp a, dfp b)
 // The accumulator as a pair, without renormalising.
 __device__ __forceinline__ dfp df_raw(dfacc A) { return {A.s, A.e}; }
 
-// Normalised pair of the accumulator (FastTwoSum).
-__device__ __forceinline__ dfp df_fin(dfacc A)
-{
-    const float h = __fadd_rn(A.s, A.e);
-    const float l = __fsub_rn(A.e, __fsub_rn(h, A.s));
-    return {h, l};
-}
-
 template <int NP>
 struct AxDfCfg {
     static constexpr int NP2 = NP * NP, NP3 = NP2 * NP;

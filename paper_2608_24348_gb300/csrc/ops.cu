@@ -85,7 +85,9 @@ int sem_ax_dev(sem_ctx *c, const void *u, void *w, double h1, double h2, sem_dty
 // range of the element-blocked factors.
 // ---------------------------------------------------------------------------
 
+#ifndef SEM_PIPE_CHUNKS
 #define SEM_PIPE_CHUNKS 8
+#endif
 
 struct AxPipe {
     cudaStream_t in, out;
