@@ -244,6 +244,47 @@ def pcg_section(ctx, sem, inputs, stream, ws, reps=1):
     return out
 
 
+def tgv_section(sem, inputs, stream, ws, warm=5, steps=30):
+    """Taylor-Green vortex Re=1600 on 32^3 undeformed elements, N=7, dt=1e-3: the
+    FP64 (A-0) and FP32-compute (A-1) policies of Table 2 with the pressure solve
+    projected onto 20 previous solutions; ms per graph-replayed step (CUDA events
+    around `steps` steps after `warm` steps from the initial state)."""
+    import torch
+
+    from paper_2608_24348_gb300 import policy
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = sem.Ctx(N_ORDER, NEL, (2 * math.pi,) * 3, (1, 1, 1))
+    xyz = torch.empty(3 * ctx.nL, dtype=torch.float64, device=dev)
+    ctx.coords(xyz)
+    x, y, z = xyz.view(3, -1)
+    ic = [t.contiguous() for t in inputs.tgv_initial(x, y, z, lib=torch)]
+    ic[2] = (ic[2] + 0 * x).contiguous()
+    del xyz
+    out = {"workload": "TGV Re=1600, 32^3 undeformed, N=7, dt=1e-3, projection 20, BDF3/EXT3 with "
+                       "3/2 dealiasing; ms per step after %d start-up steps" % warm}
+    sp = stream.cuda_stream
+    for name in ("A-0", "A-1"):
+        T = sem.TGV(ctx, 1.0 / 1600, 1e-3, vel=sem.opts(tol=1e-6, abs_tol=True),
+                    pres=sem.opts(tol=1e-4, abs_tol=True))
+        T.set_policy([policy.rule(name)])
+        T.set_projection(20)
+        T.set(*ic)
+        T.step(warm, diag=False, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        T.step(steps, diag=False, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        d = T.step(1, stream=stream)[0]
+        out[name] = {"ms_per_step": barrier_max(e0.elapsed_time(e1) / steps, ws), "ke": d["ke"],
+                     "enstrophy": d["enstrophy"], "iters": d["iters"], "status": d["status"]}
+        T.close()
+    del ic
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -291,6 +332,7 @@ def main():
     per_bf, tot_bf = time_kernel(run("bf16_tc", u32, w32), k2, 3, stream, ws)
     per_f16, tot_f16 = time_kernel(run("f16_tc", u32, w32), k2, 3, stream, ws)
     pcg = pcg_section(ctx, sem, inputs, stream, ws)
+    tgv = tgv_section(sem, inputs, stream, ws)
     clk = clocks.stop()
 
     tot64 = barrier_max(tot64, ws)
@@ -345,6 +387,7 @@ def main():
                   "sem_ax_bf16_tc_gdofs": gdof(barrier_max(tot_bf, ws) / k2),
                   "sem_ax_f16_tc_gdofs": gdof(barrier_max(tot_f16, ws) / k2)},
         "pcg": pcg,
+        "tgv": tgv,
         "e2e": {"value": ws * nL / e2e_s / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": 8 * nL,
                 "d2h_bytes_per_step": 8 * nL},
         "gpu_launches": args.steps,
