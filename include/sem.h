@@ -313,7 +313,8 @@ SEM_API int sem_tgv_set(sem_tgv *tgv, int level, const double *u, const double *
                 const double *p, int step, double t, void *stream);
 
 /* Advance nsteps P_N-P_N steps (BDF3/EXT3, 3/2-rule dealiasing).  diag: host
- * array of nsteps entries or NULL; when given, the call synchronises. */
+ * array of nsteps entries or NULL; when given, the call synchronises (after
+ * every 4096 steps at most: the device keeps a ring of 4096 log entries). */
 SEM_API int sem_tgv_step(sem_tgv *tgv, int nsteps, sem_tgv_diag *diag, void *stream);
 
 /* Copy out u^n, v^n, w^n, p^n (FP64 E-vectors; any may be NULL). */

@@ -1294,14 +1294,9 @@ static void apply_policy(sem_tgv *T, int step)
     T->cur_rule = r;
 }
 
-extern "C" int sem_tgv_step(sem_tgv *T, int nsteps, sem_tgv_diag *out, void *stream)
+// Advance nsteps steps on stream s (no synchronisation).
+static int advance(sem_tgv *T, int nsteps, cudaStream_t s)
 {
-    if (!T || nsteps < 0) return SEM_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    long long first = -1;
-    SEM_CUDA(cudaMemcpyAsync(&T->hlog[0], T->dev, sizeof(TgvDev), cudaMemcpyDeviceToHost, s));
-    SEM_CUDA(cudaStreamSynchronize(s));
-    first = ((TgvDev *)&T->hlog[0])->count;
     for (int it = 0; it < nsteps; ++it) {
         const int q = T->step + 1 < 3 ? T->step + 1 : 3;
         int rc;
@@ -1336,18 +1331,37 @@ extern "C" int sem_tgv_step(sem_tgv *T, int nsteps, sem_tgv_diag *out, void *str
         T->step += 1;
         T->t += T->dt;
     }
-    if (!out) return SEM_OK;
-    SEM_CUDA(cudaMemcpyAsync(T->hlog, T->log, sizeof(TgvLogEntry) * TGV_LOG, cudaMemcpyDeviceToHost, s));
-    SEM_CUDA(cudaStreamSynchronize(s));
+    return SEM_OK;
+}
+
+extern "C" int sem_tgv_step(sem_tgv *T, int nsteps, sem_tgv_diag *out, void *stream)
+{
+    if (!T || nsteps < 0) return SEM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!out) return advance(T, nsteps, s);
+    // the device log is a ring of TGV_LOG entries: read it back after every
+    // TGV_LOG steps at most
     int worst = SEM_OK;
-    for (int it = 0; it < nsteps; ++it) {
-        const TgvLogEntry &L = T->hlog[(first + it) % TGV_LOG];
-        out[it].t = L.t;
-        out[it].ke = L.ke;
-        out[it].enstrophy = L.en;
-        for (int k = 0; k < 4; ++k) out[it].iters[k] = L.iters[k];
-        out[it].status = L.status;
-        if (L.status != 0 && worst == SEM_OK) worst = L.status;
+    for (int done = 0; done < nsteps;) {
+        const int n = nsteps - done < TGV_LOG ? nsteps - done : TGV_LOG;
+        SEM_CUDA(cudaMemcpyAsync(&T->hlog[0], T->dev, sizeof(TgvDev), cudaMemcpyDeviceToHost, s));
+        SEM_CUDA(cudaStreamSynchronize(s));
+        const long long first = ((TgvDev *)&T->hlog[0])->count;
+        const int rc = advance(T, n, s);
+        if (rc) return rc;
+        SEM_CUDA(cudaMemcpyAsync(T->hlog, T->log, sizeof(TgvLogEntry) * TGV_LOG, cudaMemcpyDeviceToHost, s));
+        SEM_CUDA(cudaStreamSynchronize(s));
+        for (int it = 0; it < n; ++it) {
+            const TgvLogEntry &L = T->hlog[(first + it) % TGV_LOG];
+            sem_tgv_diag &D = out[done + it];
+            D.t = L.t;
+            D.ke = L.ke;
+            D.enstrophy = L.en;
+            for (int k = 0; k < 4; ++k) D.iters[k] = L.iters[k];
+            D.status = L.status;
+            if (L.status != 0 && worst == SEM_OK) worst = L.status;
+        }
+        done += n;
     }
     return worst;
 }

@@ -156,3 +156,29 @@ def test_tgv_other_orders_match_oracle(sem, N, nel):
     ref = O.step(10)
     assert e_max([r["ke"] for r in d], ref[:, 1]) <= 1e-10
     assert e_max([r["enstrophy"] for r in d], ref[:, 2]) <= 1e-9
+
+
+def test_tgv_diag_longer_than_the_device_log(sem):
+    """One call of 4100 steps (more than the 4096-entry device log ring) returns
+    the same history as calls of 4000 and 100 steps: consecutive times, equal
+    KE and enstrophy."""
+    torch, _ = torch_dev()
+    ctx, _, _ = pair(sem, 5, (2, 2, 2), 0.0, with_oracle=False)
+    logs = []
+    for split in ((4100,), (4000, 100)):
+        T = _gpu_tgv(sem, ctx, 1.0 / 100, 1e-3)
+        T.set(*_ic_gpu(ctx))
+        stream = torch.cuda.Stream()
+        d = []
+        with torch.cuda.stream(stream):
+            for n in split:
+                d += T.step(n, stream=stream)
+        T.close()
+        logs.append(d)
+    a, b = logs
+    assert len(a) == len(b) == 4100
+    assert all(r["status"] == 0 for r in a)
+    t = np.array([r["t"] for r in a])
+    assert np.allclose(np.diff(t), 1e-3, rtol=0, atol=1e-9) and abs(t[0] - 1e-3) <= 1e-12
+    assert [r["ke"] for r in a] == [r["ke"] for r in b]
+    assert [r["enstrophy"] for r in a] == [r["enstrophy"] for r in b]
