@@ -66,6 +66,21 @@ def e_peak(hist, ref) -> float:
     return float(abs(h.max() - r.max()) / np.abs(r).max())
 
 
+def peak(t, y):
+    """(time, value) of the largest sample of y(t) on a uniform time grid,
+    refined to the vertex of the parabola through it and its two neighbours
+    (the largest sample itself at either end of the record)."""
+    t, y = np.asarray(t, dtype=float), np.asarray(y, dtype=float)
+    k = int(np.argmax(y))
+    if 0 < k < len(y) - 1:
+        a, b, c = y[k - 1], y[k], y[k + 1]
+        den = a - 2 * b + c
+        if den < 0:
+            off = 0.5 * (a - c) / den
+            return float(t[k] + off * (t[k + 1] - t[k])), float(b - 0.25 * (a - c) * off)
+    return float(t[k]), float(y[k])
+
+
 def replay(configs=None, nel=32, N=7, re=1600.0, dt=1e-3, steps=200, warm=3, maxit=4000, projection=0):
     """Run each configuration from the same initial state on cuda:0; returns a
     list of dicts with ms/step of the timed steps (CUDA events around the
@@ -132,9 +147,113 @@ def replay(configs=None, nel=32, N=7, re=1600.0, dt=1e-3, steps=200, warm=3, max
     return out
 
 
+def long_run(configs=("A-0", "A-1", "B-0"), nel=32, N=7, re=1600.0, dt=4e-3, t_end=12.0, projection=20,
+             chunk=250, warm=3, maxit=4000, every=25, budget_s=None, log=None):
+    """Run each configuration from the Sec. 3 initial state to t_end (the long
+    runs behind Table 3), in chunks of `chunk` graph-replayed steps.  A run stops
+    early when a solve fails to converge, KE or enstrophy stop being finite or
+    KE exceeds its initial value, or (budget_s) the configurations together
+    have stepped for that many seconds.  Returns one dict per configuration:
+    ms/step after the `warm` start-up steps, mean and largest iteration counts,
+    the time reached, the enstrophy peak (time and value at the vertex of the
+    parabola through the largest sample and its neighbours, and the dissipation rate
+    2 nu Omega there), the dissipation rate -dKE/dt at the same time (their gap
+    is the numerical dissipation of the discretisation), and the KE / enstrophy
+    history every `every` steps; errors against A-0's history (Sec. 4.2) over
+    the steps both reached.  log, if given, is called with a one-line summary
+    after each configuration."""
+    import math
+    import time
+
+    import torch
+
+    from . import inputs, sem
+
+    configs = list(configs)
+    nu = 1.0 / re
+    nsteps = int(round(t_end / dt))
+    ctx = sem.Ctx(N, (nel,) * 3, (2 * math.pi,) * 3, (1, 1, 1))
+    xyz = torch.empty(3 * ctx.nL, dtype=torch.float64, device=torch.device("cuda:0"))
+    ctx.coords(xyz)
+    x, y, z = xyz.view(3, -1)
+    ic = [t.contiguous() for t in inputs.tgv_initial(x, y, z, lib=torch)]
+    ic[2] = (ic[2] + 0 * x).contiguous()
+    del xyz, x, y, z
+    vo = sem.opts(tol=1e-6, abs_tol=True, maxit=maxit)
+    po = sem.opts(tol=1e-4, abs_tol=True, maxit=maxit)
+    wall0 = time.time()
+    out = []
+    for name in configs:
+        T = sem.TGV(ctx, nu, dt, op="f64", vel=vo, pres=po)
+        T.set_policy([rule(name)])
+        if projection:
+            T.set_projection(projection)
+        T.set(*ic)
+        ke0 = T.energy()[0]
+        stream = torch.cuda.Stream()
+        d, ms, timed, stop = [], 0.0, 0, None
+        with torch.cuda.stream(stream):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            while len(d) < nsteps:
+                n = min(warm if not d else chunk, nsteps - len(d))
+                e0.record(stream)
+                part = T.step(n, stream=stream)
+                e1.record(stream)
+                stream.synchronize()
+                if d:  # the start-up steps are not timed
+                    ms += e0.elapsed_time(e1)
+                    timed += n
+                d += part
+                if any(r["status"] != 0 for r in part):
+                    stop = "solve status %d" % max((r["status"] for r in part), key=abs)
+                elif not all(math.isfinite(r["ke"]) and math.isfinite(r["enstrophy"]) for r in part):
+                    stop = "non-finite KE or enstrophy"
+                elif max(r["ke"] for r in part) > ke0 * (1 + 1e-6):
+                    stop = "KE above its initial value"
+                elif budget_s is not None and time.time() - wall0 > budget_s:
+                    stop = "time budget"
+                if stop:
+                    break
+        T.close()
+        t = np.array([r["t"] for r in d])
+        ke = np.array([r["ke"] for r in d])
+        en = np.array([r["enstrophy"] for r in d])
+        k = int(np.argmax(en))
+        eps_ke = -np.gradient(ke, t) if len(t) > 2 else np.full_like(ke, np.nan)
+        tp, ep = peak(t, en)
+        out.append(dict(config=name, **TABLE2[name], re=re, dt=dt, nel=nel, N=N, projection=projection,
+                        steps=len(d), t_reached=float(t[-1]) if len(t) else 0.0, stopped=stop,
+                        ms_per_step=ms / timed if timed else float("nan"),
+                        pres_iters=float(np.mean([r["iters"][0] for r in d])),
+                        pres_iters_max=int(max(r["iters"][0] for r in d)),
+                        vel_iters=float(np.mean([sum(r["iters"][1:]) / 3 for r in d])),
+                        t_peak=tp, enstrophy_peak=ep,
+                        eps_peak=float(2 * nu * en[k]), eps_ke_at_peak=float(eps_ke[k]),
+                        ke_end=float(ke[-1]), ke=ke.tolist(), enstrophy=en.tolist(),
+                        series=[[float(t[i]), float(ke[i]), float(en[i])]
+                                for i in range(every - 1, len(d), every)]))
+        if log:
+            r = out[-1]
+            log("%s: %d steps to t=%.3f (%s), %.2f ms/step, pressure it. %.1f (max %d), "
+                "enstrophy peak %.4f at t=%.3f" % (name, r["steps"], r["t_reached"], stop or "done",
+                                                    r["ms_per_step"], r["pres_iters"], r["pres_iters_max"],
+                                                    r["enstrophy_peak"], r["t_peak"]))
+    ref = next((r for r in out if r["config"] == "A-0"), None)
+    for row in out:
+        if ref is not None:
+            n = min(row["steps"], ref["steps"])
+            row["e_E_max"] = e_max(row["ke"][:n], ref["ke"][:n])
+            row["e_Omega_max"] = e_max(row["enstrophy"][:n], ref["enstrophy"][:n])
+            row["e_Omega_peak"] = e_peak(row["enstrophy"][:n], ref["enstrophy"][:n])
+    for row in out:
+        del row["ke"], row["enstrophy"]
+    return out
+
+
 def main(argv=None):
     import argparse
     import json
+    import sys
 
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--nel", type=int, default=32)
@@ -144,7 +263,22 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--configs", default=",".join(TABLE2))
     ap.add_argument("--projection", type=int, default=0)
+    ap.add_argument("--t-end", type=float, default=None,
+                    help="run each configuration to this time instead (long runs; --projection "
+                         "defaults to 20 there)")
+    ap.add_argument("--budget-s", type=float, default=None)
+    ap.add_argument("--out", default=None, help="long runs: write the rows with their histories here")
     args = ap.parse_args(argv)
+    if args.t_end is not None:
+        rows = long_run(args.configs.split(","), args.nel, args.N, args.re, args.dt, args.t_end,
+                        projection=args.projection or 20, budget_s=args.budget_s,
+                        log=lambda m: print(m, file=sys.stderr, flush=True))
+        if args.out:
+            with open(args.out, "w") as f:
+                json.dump(rows, f)
+        for r in rows:
+            print(json.dumps({k: v for k, v in r.items() if k != "series"}), flush=True)
+        return
     rows = replay(args.configs.split(","), args.nel, args.N, args.re, args.dt, args.steps,
                   projection=args.projection)
     for r in rows:

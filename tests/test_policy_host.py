@@ -78,3 +78,16 @@ def test_policy_struct_matches_the_c_header():
     assert ctypes.sizeof(sem.TgvPolicy) == 5 * ctypes.sizeof(ctypes.c_int)
     m = re.search(r"#define SEM_TGV_MAX_RULES (\d+)", text)
     assert m and int(m.group(1)) == 8
+
+
+def test_peak_is_the_vertex_of_the_parabola_through_the_top_samples():
+    t = [0.1 * i for i in range(20)]
+    # an exact parabola: the vertex is recovered between samples
+    tp, yp = policy.peak(t, [3 - (x - 0.537) ** 2 for x in t])
+    assert tp == pytest.approx(0.537, abs=1e-12) and yp == pytest.approx(3.0, abs=1e-12)
+    # a smooth non-parabolic peak: error of the three-point vertex is O(dt^3) in time
+    import math
+    tp, yp = policy.peak(t, [math.exp(-(x - 1.234) ** 2) for x in t])
+    assert abs(tp - 1.234) < 2e-3 and abs(yp - 1.0) < 1e-4
+    # a maximum at the end of the record stays the last sample
+    assert policy.peak(t, t) == (pytest.approx(1.9), pytest.approx(1.9))
