@@ -136,10 +136,13 @@ SEM_API int sem_ax(sem_ctx *ctx, const void *u, void *w, double h1, double h2, s
 /* Autotuner of sem_ax's kernel choice for the context's order N and dtype.
  * Times every candidate tile shape (for SEM_F32: 0 = direct loads, 1 =
  * bulk-copy staged, 256 threads x 2 stages, 2 = staged, 128 threads x 3
- * stages; other dtypes have one candidate) reps times on the context's solver
- * workspace (scratch between solves; no allocation), stores the fastest for
- * this process and returns it in *best; ms (may be NULL) receives the average
- * time of each candidate (-1 where a candidate does not apply).  Synchronous. */
+ * stages; for SEM_F64 with even N+1 <= 10, the folded float-pair kernel with
+ * 0 = 256/(N+1)^2 elements per block, 1 = half and 2 = a quarter of that (at
+ * least one); other cases have one candidate, reported as 0 ms) reps times on
+ * the context's solver workspace (scratch between solves; no allocation),
+ * stores the fastest for this process and returns it in *best; ms (may be
+ * NULL, else 3 entries) receives the average time of each candidate (-1 where
+ * a candidate does not apply).  Synchronous. */
 SEM_API int sem_tune_ax(sem_ctx *ctx, sem_dtype dtype, int reps, double *ms, int *best);
 
 /* Selects sem_ax's kernel for order N and dtype in this process (e.g. from a

@@ -48,9 +48,17 @@ __global__ void __launch_bounds__(AxDfCfg<NP>::THREADS, 2)
     }
 }
 
-// Folded (even-odd) variant for even NP.
-template <int NP>
-__global__ void __launch_bounds__(AxEoCfg<NP>::THREADS, 2)
+// Folded (even-odd) variant for even NP, NE elements per block.  Each block is
+// resident on the SM with at most 128 registers a thread (blocks of
+// 32 ceil(T/32) threads, 512 per SM at that register count).
+template <int NP, int NE>
+struct DfeoShape {
+    static constexpr int THREADS = NE * NP * NP;
+    static constexpr int MINB = 16 / ((THREADS + 31) / 32) > 0 ? 16 / ((THREADS + 31) / 32) : 1;
+};
+
+template <int NP, int NE>
+__global__ void __launch_bounds__(DfeoShape<NP, NE>::THREADS, DfeoShape<NP, NE>::MINB)
     k_ax_dfeo(const double *__restrict__ u, double *__restrict__ w, const dfp *__restrict__ geo,
               const dfp *__restrict__ tabs, dfp h1, dfp h2, int64_t E)
 {
@@ -59,12 +67,12 @@ __global__ void __launch_bounds__(AxEoCfg<NP>::THREADS, 2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     dfp *sm = reinterpret_cast<dfp *>(smem_raw);
     dfp *stab = sm;
-    int *sexp = reinterpret_cast<int *>(sm + 4 * HH + (size_t)C::NE * 5 * C::SLAB);
+    int *sexp = reinterpret_cast<int *>(sm + 4 * HH + (size_t)NE * 5 * C::SLAB);
     const int grp = threadIdx.x / C::NP2, tid = threadIdx.x - grp * C::NP2;
     dfp *slab = sm + 4 * HH + (size_t)grp * 5 * C::SLAB;
     for (int t = threadIdx.x; t < 4 * HH; t += blockDim.x) stab[t] = tabs[t];
-    for (int64_t e0 = (int64_t)blockIdx.x * C::NE; e0 < E; e0 += (int64_t)gridDim.x * C::NE) {
-        df_prefetch<NP>(u, geo, e0, e0 + (int64_t)gridDim.x * C::NE, C::NE, E);
+    for (int64_t e0 = (int64_t)blockIdx.x * NE; e0 < E; e0 += (int64_t)gridDim.x * NE) {
+        df_prefetch<NP>(u, geo, e0, e0 + (int64_t)gridDim.x * NE, NE, E);
         const int64_t e = e0 + grp;
         const bool active = e < E;
         const int64_t off = (active ? e : 0) * C::NP3;
@@ -77,26 +85,36 @@ __global__ void __launch_bounds__(AxEoCfg<NP>::THREADS, 2)
     }
 }
 
-template <int NP>
+template <int NP, int NE>
 static int launch_dfeo(const sem_ctx *c, const double *u, double *w, dfp H1, dfp H2, cudaStream_t s)
 {
-    using C = AxEoCfg<NP>;
-    const size_t smem = ax_dfeo_smem_bytes<NP>();
+    constexpr int T = DfeoShape<NP, NE>::THREADS;
+    const size_t smem = ax_dfeo_smem_bytes_ne<NP, NE>();
     static bool attr = false;
     if (!attr) {
-        SEM_CUDA(cudaFuncSetAttribute(k_ax_dfeo<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SEM_CUDA(cudaFuncSetAttribute(k_ax_dfeo<NP, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
     int per_sm = 0;
-    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_dfeo<NP>, C::THREADS, smem));
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_dfeo<NP, NE>, T, smem));
     if (per_sm < 1) return SEM_ERR_ARG;
-    int64_t groups = sem_ceil_div(c->E, C::NE);
+    int64_t groups = sem_ceil_div(c->E, NE);
     int64_t grid = (int64_t)per_sm * c->num_sms;
     if (grid > groups) grid = groups;
-    k_ax_dfeo<NP><<<(unsigned)grid, C::THREADS, smem, s>>>(u, w, (const dfp *)c->geodf,
-                                                          (const dfp *)c->tabdfeo, H1, H2, c->E);
+    k_ax_dfeo<NP, NE><<<(unsigned)grid, T, smem, s>>>(u, w, (const dfp *)c->geodf,
+                                                      (const dfp *)c->tabdfeo, H1, H2, c->E);
     SEM_CHECK_LAUNCH();
     return SEM_OK;
+}
+
+// Elements per block of the folded kernel's tile-shape candidates: 0 = AxEoCfg's
+// (256 threads at most), 1 and 2 = a half and a quarter of it, for N+1 <= 10.
+template <int NP>
+constexpr int dfeo_ne(int variant)
+{
+    constexpr int NE0 = AxEoCfg<NP>::NE;
+    const int ne = variant == 1 ? NE0 / 2 : variant == 2 ? NE0 / 4 : NE0;
+    return NP > 10 || ne < 1 ? NE0 : ne;
 }
 
 template <int NP>
@@ -106,7 +124,12 @@ static int launch_df(const sem_ctx *c, const double *u, double *w, double h1, do
     if constexpr (AxEoCfg<NP>::OK) {
         if (ax_dfeo_smem_bytes<NP>() <= 227 * 1024) {
             const float a = (float)h1, b = (float)h2;
-            return launch_dfeo<NP>(c, u, w, {a, (float)(h1 - (double)a)}, {b, (float)(h2 - (double)b)}, s);
+            const dfp H1 = {a, (float)(h1 - (double)a)}, H2 = {b, (float)(h2 - (double)b)};
+            const int v = sem_ax_variant(c->N, SEM_F64);
+            constexpr int N1 = dfeo_ne<NP>(1), N2 = dfeo_ne<NP>(2);
+            if (v == 1 && N1 != AxEoCfg<NP>::NE) return launch_dfeo<NP, N1>(c, u, w, H1, H2, s);
+            if (v == 2 && N2 != N1) return launch_dfeo<NP, N2>(c, u, w, H1, H2, s);
+            return launch_dfeo<NP, AxEoCfg<NP>::NE>(c, u, w, H1, H2, s);
         }
     }
     using C = AxDfCfg<NP>;

@@ -32,12 +32,18 @@ struct AxEoCfg {
     static constexpr int SLAB = NP2 * LS;       // float pairs per slab
 };
 
-// Half tables: A, B of D (gradient) and AT, BT of D^T (transpose), H*H each.
+// Half tables: A, B of D (gradient) and AT, BT of D^T (transpose), H*H each,
+// then NE elements' slabs and exponents.
+template <int NP, int NE>
+__host__ __device__ constexpr size_t ax_dfeo_smem_bytes_ne()
+{
+    return sizeof(dfp) * (4 * (NP / 2) * (NP / 2) + (size_t)NE * 5 * NP * NP * (NP + 1)) + sizeof(int) * NE;
+}
+
 template <int NP>
 __host__ __device__ constexpr size_t ax_dfeo_smem_bytes()
 {
-    return sizeof(dfp) * (4 * (NP / 2) * (NP / 2) + (size_t)AxEoCfg<NP>::NE * 5 * NP * NP * (NP + 1)) +
-           sizeof(int) * AxEoCfg<NP>::NE;
+    return ax_dfeo_smem_bytes_ne<NP, AxEoCfg<NP>::NE>();
 }
 
 __device__ __forceinline__ dfp df_neg(dfp a) { return {-a.hi, -a.lo}; }

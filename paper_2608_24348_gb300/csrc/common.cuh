@@ -115,3 +115,5 @@ int sem_stage_in(sem_ctx *ctx, const void *p, size_t bytes, int slot, cudaStream
                  const void **dev, int *is_host);
 int sem_stage_out_ptr(sem_ctx *ctx, void *p, size_t bytes, int slot, void **dev, int *is_host);
 int sem_is_device_ptr(const void *p);
+// the stand-alone operator's tile-shape candidate in force for order N and dtype
+int sem_ax_variant(int N, sem_dtype dt);

@@ -40,7 +40,8 @@ int sem_ax_variant(int N, sem_dtype dt)
 extern "C" int sem_set_ax_variant(int N, sem_dtype dt, int variant)
 {
     if (N < 1 || N > SEM_NMAX || dt < SEM_F64 || dt > SEM_F64_NATIVE) return SEM_ERR_ARG;
-    if (variant < 0 || variant >= SEM_NVARIANT || (dt != SEM_F32 && variant != 0)) return SEM_ERR_ARG;
+    if (variant < 0 || variant >= SEM_NVARIANT || (dt != SEM_F32 && dt != SEM_F64 && variant != 0))
+        return SEM_ERR_ARG;
     g_variant[N][dt] = variant;
     g_variant_set[N][dt] = 1;
     return SEM_OK;
@@ -56,8 +57,6 @@ GsDesc sem_gs_desc(const sem_ctx *c)
     d.nG = c->nG;
     return d;
 }
-
-int sem_ax_variant(int N, sem_dtype dt);
 
 // Device-pointer form (used by the stepper as well).
 int sem_ax_dev(sem_ctx *c, const void *u, void *w, double h1, double h2, sem_dtype dt,
@@ -320,35 +319,48 @@ extern "C" int sem_tune_ax(sem_ctx *c, sem_dtype dt, int reps, double *ms, int *
 {
     if (!c || !best || dt < SEM_F64 || dt > SEM_F64_NATIVE) return SEM_ERR_ARG;
     if (reps < 1) reps = 5;
-    const int nvar = dt == SEM_F32 ? SEM_NVARIANT : 1;
-    // the solver workspace of slot 0 serves as input and output (its contents
-    // are scratch between solves); u = r32, w = w32
-    const float *u = c->ws[0].r32;
-    float *w = c->ws[0].w32;
+    // FP32: three tile shapes; FP64-accurate, even N+1 <= 10: three elements-per-block
+    // counts of the folded kernel; otherwise one candidate
+    const int nvar = dt == SEM_F32 || (dt == SEM_F64 && c->n % 2 == 0 && c->n <= 10) ? SEM_NVARIANT : 1;
+    if (ms)
+        for (int v = 0; v < SEM_NVARIANT; ++v) ms[v] = -1.0;
+    if (nvar == 1) {
+        *best = 0;
+        if (ms) ms[0] = 0.0;
+        return sem_set_ax_variant(c->N, dt, 0);
+    }
+    // the solver workspace of slot 0 (allocated by sem_setup) serves as input
+    // and output, its contents being scratch between solves: r and w
+    // (FP64-accurate) or r32 and w32 (FP32); u = 0 (the kernels' instruction
+    // streams and memory traffic do not depend on the values)
+    if (!c->ws[0].r || !c->ws[0].r32) return SEM_ERR_ARG;
+    const void *u = dt == SEM_F32 ? (const void *)c->ws[0].r32 : (const void *)c->ws[0].r;
+    void *w = dt == SEM_F32 ? (void *)c->ws[0].w32 : (void *)c->ws[0].w;
     cudaStream_t s = 0;
     cudaEvent_t e0, e1;
     SEM_CUDA(cudaEventCreate(&e0));
     SEM_CUDA(cudaEventCreate(&e1));
-    SEM_CUDA(cudaMemsetAsync((void *)u, 0, sizeof(float) * c->nL, s));
+    SEM_CUDA(cudaMemsetAsync((void *)u, 0, (dt == SEM_F32 ? sizeof(float) : sizeof(double)) * c->nL, s));
+    const int saved = sem_ax_variant(c->N, dt);
+    auto run = [&](int v) {
+        if (dt == SEM_F32)
+            return sem_launch_ax_f32_variant(c, v, (const float *)u, (float *)w, 1.0f, 1.0f, s);
+        int rc = sem_set_ax_variant(c->N, dt, v);
+        return rc ? rc : sem_launch_ax_df(c, (const double *)u, (double *)w, 1.0, 1.0, s);
+    };
     double best_ms = 1e300;
     int bi = 0;
     for (int v = 0; v < nvar; ++v) {
         double t = 1e300;
-        int rc = SEM_OK;
-        if (dt == SEM_F32) {
-            rc = sem_launch_ax_f32_variant(c, v, u, w, 1.0f, 1.0f, s);  // warm-up
-            if (rc == SEM_OK) {
-                SEM_CUDA(cudaEventRecord(e0, s));
-                for (int k = 0; k < reps && rc == SEM_OK; ++k)
-                    rc = sem_launch_ax_f32_variant(c, v, u, w, 1.0f, 1.0f, s);
-                SEM_CUDA(cudaEventRecord(e1, s));
-                SEM_CUDA(cudaEventSynchronize(e1));
-                float f = 0.f;
-                SEM_CUDA(cudaEventElapsedTime(&f, e0, e1));
-                t = f / reps;
-            }
-        } else {
-            t = 0.0;
+        int rc = run(v);  // warm-up
+        if (rc == SEM_OK) {
+            SEM_CUDA(cudaEventRecord(e0, s));
+            for (int k = 0; k < reps && rc == SEM_OK; ++k) rc = run(v);
+            SEM_CUDA(cudaEventRecord(e1, s));
+            SEM_CUDA(cudaEventSynchronize(e1));
+            float f = 0.f;
+            SEM_CUDA(cudaEventElapsedTime(&f, e0, e1));
+            t = f / reps;
         }
         if (ms) ms[v] = rc == SEM_OK ? t : -1.0;
         if (rc == SEM_OK && t < best_ms) {
@@ -358,6 +370,10 @@ extern "C" int sem_tune_ax(sem_ctx *c, sem_dtype dt, int reps, double *ms, int *
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (best_ms == 1e300) {
+        sem_set_ax_variant(c->N, dt, saved);
+        return SEM_ERR_CUDA;
+    }
     *best = bi;
     return sem_set_ax_variant(c->N, dt, bi);
 }

@@ -326,7 +326,7 @@ def autotune(ctx, dtype="f32", reps=5, cache=None):
     ms = (ctypes.c_double * 8)(*([-1.0] * 8))
     best = ctypes.c_int()
     _check(L.sem_tune_ax(ctx.handle, dt, int(reps), ms, ctypes.byref(best)), "sem_tune_ax")
-    out = {"variant": best.value, "ms": [ms[i] for i in range(3 if dt == F32 else 1)]}
+    out = {"variant": best.value, "ms": [ms[i] for i in range(3) if ms[i] >= 0]}
     if cache:
         table[key] = out
         os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
