@@ -21,7 +21,11 @@
  *    (pinned or pageable); host buffers are staged through device buffers
  *    owned by the context, allocated on the first such call (sem_ax also
  *    creates two streams and a few events then, and overlaps the copies of
- *    its element chunks with the operator on the other chunks).
+ *    its element chunks with the operator on the other chunks).  Exception:
+ *    sem_ax with SEM_F64 on pinned host buffers runs the operator on the
+ *    mapped host memory itself (the kernel's loads and stores cross the host
+ *    link; no staging).  Host-pointer calls return after the result is in
+ *    place.
  *  - The caller owns every field buffer.  The library owns the geometry and
  *    the solver workspaces; it allocates only in sem_setup, sem_tgv_init and
  *    the first host-pointer call, never inside a device-pointer hot call.

@@ -9,7 +9,8 @@
 // its next group (read at that group's start).  Elements are clipped to E.
 // Prefetching the next group's geometry as well (a whole group ahead) was
 // slower (0.468 vs 0.427 ms at 32^3, N=7) and L2 evicted a third of those
-// lines before use (37% more DRAM reads).
+// lines before use (37% more DRAM reads).  u == nullptr skips the u prefetch
+// (u in mapped host memory, read over the host link by the loads themselves).
 template <int NP>
 __device__ __forceinline__ void df_prefetch(const double *u, const dfp *geo, int64_t e0, int64_t en,
                                             int ne, int64_t E)
@@ -17,13 +18,13 @@ __device__ __forceinline__ void df_prefetch(const double *u, const dfp *geo, int
     constexpr int64_t NP3 = NP * NP * NP;
     if (threadIdx.x != 0) return;
     if (e0 < E) l2_prefetch_span(geo, e0 * 7 * NP3 * 8, (e0 + ne < E ? e0 + ne : E) * 7 * NP3 * 8);
-    if (en < E) l2_prefetch_span(u, en * NP3 * 8, (en + ne < E ? en + ne : E) * NP3 * 8);
+    if (u && en < E) l2_prefetch_span(u, en * NP3 * 8, (en + ne < E ? en + ne : E) * NP3 * 8);
 }
 
 template <int NP>
 __global__ void __launch_bounds__(AxDfCfg<NP>::THREADS, 2)
     k_ax_df(const double *__restrict__ u, double *__restrict__ w, const dfp *__restrict__ geo,
-            const dfp *__restrict__ D, dfp h1, dfp h2, int64_t E)
+            const dfp *__restrict__ D, dfp h1, dfp h2, int64_t E, const double *upf)
 {
     using C = AxDfCfg<NP>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(AxDfCfg<NP>::THREADS, 2)
     dfp *svr = su + C::NP3, *svs = svr + C::NP3;
     ax_df_load_D<NP>(D, sD, sDT);
     for (int64_t e0 = (int64_t)blockIdx.x * C::NE; e0 < E; e0 += (int64_t)gridDim.x * C::NE) {
-        df_prefetch<NP>(u, geo, e0, e0 + (int64_t)gridDim.x * C::NE, C::NE, E);
+        df_prefetch<NP>(upf, geo, e0, e0 + (int64_t)gridDim.x * C::NE, C::NE, E);
         const int64_t e = e0 + grp;
         const bool active = e < E;
         const int64_t off = (active ? e : 0) * C::NP3;
@@ -60,7 +61,7 @@ struct DfeoShape {
 template <int NP, int NE>
 __global__ void __launch_bounds__(DfeoShape<NP, NE>::THREADS, DfeoShape<NP, NE>::MINB)
     k_ax_dfeo(const double *__restrict__ u, double *__restrict__ w, const dfp *__restrict__ geo,
-              const dfp *__restrict__ tabs, dfp h1, dfp h2, int64_t E)
+              const dfp *__restrict__ tabs, dfp h1, dfp h2, int64_t E, const double *upf)
 {
     using C = AxEoCfg<NP>;
     constexpr int HH = (NP / 2) * (NP / 2);
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(DfeoShape<NP, NE>::THREADS, DfeoShape<NP, NE>:
     dfp *slab = sm + 4 * HH + (size_t)grp * 5 * C::SLAB;
     for (int t = threadIdx.x; t < 4 * HH; t += blockDim.x) stab[t] = tabs[t];
     for (int64_t e0 = (int64_t)blockIdx.x * NE; e0 < E; e0 += (int64_t)gridDim.x * NE) {
-        df_prefetch<NP>(u, geo, e0, e0 + (int64_t)gridDim.x * NE, NE, E);
+        df_prefetch<NP>(upf, geo, e0, e0 + (int64_t)gridDim.x * NE, NE, E);
         const int64_t e = e0 + grp;
         const bool active = e < E;
         const int64_t off = (active ? e : 0) * C::NP3;
@@ -102,7 +103,8 @@ static int launch_dfeo(const sem_ctx *c, const double *u, double *w, dfp H1, dfp
     int64_t grid = (int64_t)per_sm * c->num_sms;
     if (grid > groups) grid = groups;
     k_ax_dfeo<NP, NE><<<(unsigned)grid, T, smem, s>>>(u, w, (const dfp *)c->geodf,
-                                                      (const dfp *)c->tabdfeo, H1, H2, c->E);
+                                                      (const dfp *)c->tabdfeo, H1, H2, c->E,
+                                                      c->u_sysmem ? nullptr : u);
     SEM_CHECK_LAUNCH();
     return SEM_OK;
 }
@@ -148,7 +150,8 @@ static int launch_df(const sem_ctx *c, const double *u, double *w, double h1, do
     const float h1h = (float)h1, h2h = (float)h2;
     const dfp H1 = {h1h, (float)(h1 - (double)h1h)}, H2 = {h2h, (float)(h2 - (double)h2h)};
     k_ax_df<NP><<<(unsigned)grid, C::THREADS, smem, s>>>(u, w, (const dfp *)c->geodf,
-                                                        (const dfp *)c->tabdf, H1, H2, c->E);
+                                                        (const dfp *)c->tabdf, H1, H2, c->E,
+                                                        c->u_sysmem ? nullptr : u);
     SEM_CHECK_LAUNCH();
     return SEM_OK;
 }

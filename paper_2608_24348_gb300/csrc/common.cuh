@@ -75,6 +75,7 @@ struct sem_ctx {
     void *stage[2];
     size_t stage_bytes;
     void *pipe;           // streams and events of the pipelined host-buffer sem_ax (lazy)
+    int u_sysmem;         // sem_ax's u is mapped host memory: no L2 bulk prefetch of it
 };
 
 static inline int64_t sem_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

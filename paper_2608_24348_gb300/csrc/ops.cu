@@ -178,6 +178,38 @@ static int ax_host(sem_ctx *c, const void *u, void *w, bool uh, bool wh, double 
     return SEM_OK;
 }
 
+// The device address of pinned (page-locked, mapped) host memory, else null.
+// Under unified addressing every pinned allocation is mapped; on GB300 the
+// Grace memory behind it is reached coherently over NVLink-C2C.
+static void *mapped_host(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// FP64-accurate operator on pinned host buffers without staging copies: the
+// kernel's own loads and stores cross the host link (its u prefetch into L2 is
+// off), so transfer and arithmetic overlap at the granularity of the loads.
+static int ax_mapped(sem_ctx *c, const void *u, void *w, bool uh, bool wh, double h1, double h2,
+                     cudaStream_t s, bool *done)
+{
+    *done = false;
+    const void *du = uh ? mapped_host(u) : u;
+    void *dw = wh ? mapped_host(w) : w;
+    if (!du || !dw || ((uintptr_t)du | (uintptr_t)dw) % sizeof(double)) return SEM_OK;
+    sem_ctx sub = *c;
+    sub.u_sysmem = uh ? 1 : 0;
+    int rc = sem_ax_dev(&sub, du, dw, h1, h2, SEM_F64, s);
+    if (rc) return rc;
+    SEM_CUDA(cudaStreamSynchronize(s));
+    *done = true;
+    return SEM_OK;
+}
+
 extern "C" int sem_ax(sem_ctx *c, const void *u, void *w, double h1, double h2, sem_dtype dt,
                       void *stream)
 {
@@ -185,7 +217,14 @@ extern "C" int sem_ax(sem_ctx *c, const void *u, void *w, double h1, double h2, 
     if (dt < SEM_F64 || dt > SEM_F64_NATIVE) return SEM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const bool uh = !sem_is_device_ptr(u), wh = !sem_is_device_ptr(w);
-    if (uh || wh) return ax_host(c, u, w, uh, wh, h1, h2, dt, s);
+    if (uh || wh) {
+        if (dt == SEM_F64) {
+            bool done = false;
+            int rc = ax_mapped(c, u, w, uh, wh, h1, h2, s, &done);
+            if (rc || done) return rc;
+        }
+        return ax_host(c, u, w, uh, wh, h1, h2, dt, s);
+    }
     return sem_ax_dev(c, u, w, h1, h2, dt, s);
 }
 

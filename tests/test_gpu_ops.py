@@ -164,8 +164,10 @@ def test_ax_host_pointers(sem):
 @pytest.mark.parametrize("dt", ["f64", "f64_native", "f32", "bf16_tc"])
 def test_ax_host_pipeline_equals_device_call(sem, dt):
     """Host buffers run the operator in element chunks with overlapped copies
-    (45 elements: 8 chunks of 6, the last one ragged); every element's result is
-    bit-identical to the device-pointer call, for host/device mixes too."""
+    (45 elements: 8 chunks of 6, the last one ragged), or, for the FP64-accurate
+    operator on pinned buffers, on the mapped host memory directly; every
+    element's result is bit-identical to the device-pointer call, for
+    host/device mixes too."""
     torch, dev = torch_dev()
     ctx, _, _ = make(sem, 7, (3, 3, 5), 0.1)
     u = inputs.local_uniform_field(ctx.nL, seed=11)
@@ -177,10 +179,30 @@ def test_ax_host_pipeline_equals_device_call(sem, dt):
     ref = wd.cpu().numpy()
     uh = torch.from_numpy(u).pin_memory()
     for src, dst in ((uh, torch.empty_like(uh).pin_memory()), (u, np.zeros_like(u)),
-                     (uh, torch.empty_like(ud)), (ud, np.zeros_like(u))):
+                     (uh, torch.empty_like(ud)), (ud, np.zeros_like(u)),
+                     (ud, torch.empty_like(uh).pin_memory())):
         ctx.ax(src, dst, 0.3, 5.0, dt)
         got = dst.cpu().numpy() if isinstance(dst, torch.Tensor) else dst
         assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("N,nel", [(4, (3, 2, 5)), (8, (2, 3, 3))])
+def test_ax_f64_on_pinned_host_memory(sem, N, nel):
+    """The FP64-accurate operator reads pinned host u and writes pinned host w in
+    place (unfolded kernel for odd N+1, folded for even): within the FP64 bar of
+    the oracle and bit-identical to the device call."""
+    torch, dev = torch_dev()
+    ctx, m, _ = make(sem, N, nel, 0.1)
+    u = inputs.local_uniform_field(ctx.nL, seed=12)
+    ud = torch.from_numpy(u).to(dev)
+    wd = torch.empty_like(ud)
+    ctx.ax(ud, wd, 0.7, 3.0, "f64")
+    uh = torch.from_numpy(u).pin_memory()
+    wh = torch.full_like(uh, float("nan")).pin_memory()
+    ctx.ax(uh, wh, 0.7, 3.0, "f64")
+    assert np.array_equal(wh.numpy(), wd.cpu().numpy())
+    assert rel_err(wh.numpy(), m.ax(u, 0.7, 3.0)) <= 1e-12
+    assert ctx.device_status() == 0
 
 
 def test_ax_empty_input_is_rejected(sem):
