@@ -347,7 +347,9 @@ def main():
     avg32 = statistics.mean(per32)
     hbm = lambda B, ms: B * nL / (ms * 1e-3) / 1e9
 
-    # end to end through the C ABI with pinned host buffers (H2D of u, D2H of w)
+    # end to end through the C ABI with pinned host buffers: u comes from and w
+    # returns to host memory inside every call (the FP64-accurate operator reads
+    # and writes the mapped host memory over the host link itself)
     uh = torch.from_numpy(u_h).pin_memory()
     wh = torch.empty_like(uh).pin_memory()
     ctx.ax(uh, wh, H1, H2, "f64", stream=sp)
