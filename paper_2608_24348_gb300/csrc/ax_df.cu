@@ -91,11 +91,8 @@ static int launch_dfeo(const sem_ctx *c, const double *u, double *w, dfp H1, dfp
 {
     constexpr int T = DfeoShape<NP, NE>::THREADS;
     const size_t smem = ax_dfeo_smem_bytes_ne<NP, NE>();
-    static bool attr = false;
-    if (!attr) {
-        SEM_CUDA(cudaFuncSetAttribute(k_ax_dfeo<NP, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<unsigned> attr{0};
+    SEM_CUDA(sem_smem_attr(k_ax_dfeo<NP, NE>, smem, attr));
     int per_sm = 0;
     SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_dfeo<NP, NE>, T, smem));
     if (per_sm < 1) return SEM_ERR_ARG;
@@ -136,11 +133,8 @@ static int launch_df(const sem_ctx *c, const double *u, double *w, double h1, do
     }
     using C = AxDfCfg<NP>;
     const size_t smem = ax_df_smem_bytes<NP>();
-    static bool attr = false;
-    if (!attr) {
-        SEM_CUDA(cudaFuncSetAttribute(k_ax_df<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<unsigned> attr{0};
+    SEM_CUDA(sem_smem_attr(k_ax_df<NP>, smem, attr));
     int per_sm = 0;
     SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_df<NP>, C::THREADS, smem));
     if (per_sm < 1) per_sm = 1;

@@ -117,11 +117,8 @@ static int launch_tma(const sem_ctx *c, const float *u, float *w, float h1, floa
         return SEM_ERR_ARG;
     } else {
         auto kern = k_ax_tma<NP, TH, ST>;
-        static bool attr = false;
-        if (!attr) {
-            SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM));
-            attr = true;
-        }
+        static std::atomic<unsigned> attr{0};
+        SEM_CUDA(sem_smem_attr(kern, T::SMEM, attr));
         int per_sm = 0;
         SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T::THREADS, T::SMEM));
         if (per_sm < 1) return SEM_ERR_ARG;

@@ -40,12 +40,8 @@ int launch_ax(const sem_ctx *c, const T *u, T *w, const T *geo, const T *D, T h1
 {
     using C = AxCfg<NP>;
     size_t smem = ax_smem_bytes<NP, T>();
-    static bool attr_done = false;
-    if (!attr_done) {
-        SEM_CUDA(cudaFuncSetAttribute(k_ax<NP, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        attr_done = true;
-    }
+    static std::atomic<unsigned> attr{0};
+    SEM_CUDA(sem_smem_attr(k_ax<NP, T>, smem, attr));
     int per_sm = 0;
     SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax<NP, T>, C::THREADS, smem));
     if (per_sm < 1) per_sm = 1;

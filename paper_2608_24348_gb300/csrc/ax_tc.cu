@@ -23,12 +23,8 @@ static int launch_tc(const sem_ctx *c, const float *u, float *w, float h1, float
         return SEM_ERR_ARG;
     } else {
         const size_t smem = ax_tc_smem_bytes<NP>();
-        static bool attr = false;
-        if (!attr) {
-            SEM_CUDA(cudaFuncSetAttribute(k_ax_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            attr = true;
-        }
+        static std::atomic<unsigned> attr{0};
+        SEM_CUDA(sem_smem_attr(k_ax_tc<NP>, smem, attr));
         int per_sm = 0;
         SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_tc<NP>, 256, smem));
         if (per_sm < 1) per_sm = 1;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "sem.h"
 
 #define SEM_NMAX 15
@@ -79,6 +81,22 @@ struct sem_ctx {
 };
 
 static inline int64_t sem_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Raises a kernel's dynamic shared-memory limit to smem once per device: done
+// holds one bit per device ordinal (0..31) and is set only after success, so
+// concurrent first calls at worst both set the attribute.
+template <class K>
+static inline cudaError_t sem_smem_attr(K *kernel, size_t smem, std::atomic<unsigned> &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned bit = 1u << (dev & 31);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 // ---------------------------------------------------------------------------
 // Compile-time dispatch on NP = N + 1

@@ -1024,11 +1024,8 @@ int launch_solve(const SolveParams<MAXP> &prm, int num_sms, long long max_items,
 {
     auto kern = k_solve<MAXP, MODE, NPs...>;
     const size_t smem = SmemMax<MODE, NPs...>::v;
-    static bool attr = false;
-    if (!attr) {
-        SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<unsigned> attr{0};
+    SEM_CUDA(sem_smem_attr(kern, smem, attr));
     int per_sm = 0;
     SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SEM_SOLVE_THREADS, smem));
     if (per_sm < 1) return SEM_ERR_ARG;

@@ -636,11 +636,8 @@ static size_t conv_smem(bool f32)
 template <int NP, typename T, int R16>
 static int run_convect(const ConvArgs &a, int grid, size_t smem, cudaStream_t s)
 {
-    static bool attr = false;
-    if (!attr) {
-        SEM_CUDA(cudaFuncSetAttribute(k_convect<NP, T, R16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<unsigned> attr{0};
+    SEM_CUDA(sem_smem_attr(k_convect<NP, T, R16>, smem, attr));
     k_convect<NP, T, R16><<<grid, 256, smem, s>>>(a);
     SEM_CHECK_LAUNCH();
     return SEM_OK;
