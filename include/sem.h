@@ -141,8 +141,10 @@ SEM_API int sem_ax(sem_ctx *ctx, const void *u, void *w, double h1, double h2, s
  * Times every candidate tile shape (for SEM_F32: 0 = direct loads, 1 =
  * bulk-copy staged, 256 threads x 2 stages, 2 = staged, 128 threads x 3
  * stages; for SEM_F64 with even N+1 <= 10, the folded float-pair kernel with
- * 0 = 256/(N+1)^2 elements per block, 1 = half and 2 = a quarter of that (at
- * least one); other cases have one candidate, reported as 0 ms) reps times on
+ * 0 = 256/(N+1)^2 elements per block and block-wide barriers, 1 = the same
+ * with one hardware barrier per element where (N+1)^2 is a multiple of 32
+ * (else as 0), 2 = half the elements per block (at least one); other cases
+ * have one candidate, reported as 0 ms) reps times on
  * the context's solver workspace (scratch between solves; no allocation),
  * stores the fastest for this process and returns it in *best; ms (may be
  * NULL, else 3 entries) receives the average time of each candidate (-1 where

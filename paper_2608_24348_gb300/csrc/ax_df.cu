@@ -58,7 +58,7 @@ struct DfeoShape {
     static constexpr int MINB = 16 / ((THREADS + 31) / 32) > 0 ? 16 / ((THREADS + 31) / 32) : 1;
 };
 
-template <int NP, int NE>
+template <int NP, int NE, int GS>
 __global__ void __launch_bounds__(DfeoShape<NP, NE>::THREADS, DfeoShape<NP, NE>::MINB)
     k_ax_dfeo(const double *__restrict__ u, double *__restrict__ w, const dfp *__restrict__ geo,
               const dfp *__restrict__ tabs, dfp h1, dfp h2, int64_t E, const double *upf)
@@ -72,6 +72,8 @@ __global__ void __launch_bounds__(DfeoShape<NP, NE>::THREADS, DfeoShape<NP, NE>:
     const int grp = threadIdx.x / C::NP2, tid = threadIdx.x - grp * C::NP2;
     dfp *slab = sm + 4 * HH + (size_t)grp * 5 * C::SLAB;
     for (int t = threadIdx.x; t < 4 * HH; t += blockDim.x) stab[t] = tabs[t];
+    // with block barriers the element's first barrier publishes the tables
+    if constexpr (GS != 0) __syncthreads();
     for (int64_t e0 = (int64_t)blockIdx.x * NE; e0 < E; e0 += (int64_t)gridDim.x * NE) {
         df_prefetch<NP>(upf, geo, e0, e0 + (int64_t)gridDim.x * NE, NE, E);
         const int64_t e = e0 + grp;
@@ -81,39 +83,49 @@ __global__ void __launch_bounds__(DfeoShape<NP, NE>::THREADS, DfeoShape<NP, NE>:
         double *we = w + off;
         auto load = [&](int p) { return ue[p]; };
         auto store = [&](int p, double v) { we[p] = v; };
-        ax_dfeo_element<NP>(load, store, geo + (active ? e : 0) * 7 * C::NP3, h1, h2, stab, slab,
-                            sexp + grp, tid, active);
+        ax_dfeo_element<NP, GS>(load, store, geo + (active ? e : 0) * 7 * C::NP3, h1, h2, stab, slab,
+                                sexp + grp, tid, active, grp);
     }
 }
 
-template <int NP, int NE>
+template <int NP, int NE, int GS>
 static int launch_dfeo(const sem_ctx *c, const double *u, double *w, dfp H1, dfp H2, cudaStream_t s)
 {
     constexpr int T = DfeoShape<NP, NE>::THREADS;
     const size_t smem = ax_dfeo_smem_bytes_ne<NP, NE>();
     static std::atomic<unsigned> attr{0};
-    SEM_CUDA(sem_smem_attr(k_ax_dfeo<NP, NE>, smem, attr));
+    SEM_CUDA(sem_smem_attr(k_ax_dfeo<NP, NE, GS>, smem, attr));
     int per_sm = 0;
-    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_dfeo<NP, NE>, T, smem));
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_dfeo<NP, NE, GS>, T, smem));
     if (per_sm < 1) return SEM_ERR_ARG;
     int64_t groups = sem_ceil_div(c->E, NE);
     int64_t grid = (int64_t)per_sm * c->num_sms;
     if (grid > groups) grid = groups;
-    k_ax_dfeo<NP, NE><<<(unsigned)grid, T, smem, s>>>(u, w, (const dfp *)c->geodf,
+    k_ax_dfeo<NP, NE, GS><<<(unsigned)grid, T, smem, s>>>(u, w, (const dfp *)c->geodf,
                                                       (const dfp *)c->tabdfeo, H1, H2, c->E,
                                                       c->u_sysmem ? nullptr : u);
     SEM_CHECK_LAUNCH();
     return SEM_OK;
 }
 
-// Elements per block of the folded kernel's tile-shape candidates: 0 = AxEoCfg's
-// (256 threads at most), 1 and 2 = a half and a quarter of it, for N+1 <= 10.
+// Tile-shape candidates of the folded kernel (N+1 <= 10): 0 = AxEoCfg's
+// elements per block (256 threads at most) with block barriers; 1 = the same
+// with one named barrier per element group where a group is whole warps
+// ((N+1)^2 a multiple of 32, 2..15 groups), else as 0; 2 = half the elements
+// per block.
 template <int NP>
 constexpr int dfeo_ne(int variant)
 {
     constexpr int NE0 = AxEoCfg<NP>::NE;
-    const int ne = variant == 1 ? NE0 / 2 : variant == 2 ? NE0 / 4 : NE0;
+    const int ne = variant == 2 ? NE0 / 2 : NE0;
     return NP > 10 || ne < 1 ? NE0 : ne;
+}
+
+template <int NP>
+constexpr int dfeo_group_sync()
+{
+    constexpr int NE0 = AxEoCfg<NP>::NE;
+    return (NP * NP) % 32 == 0 && NE0 >= 2 && NE0 <= 15 && NP <= 10 ? NP * NP : 0;
 }
 
 template <int NP>
@@ -125,10 +137,10 @@ static int launch_df(const sem_ctx *c, const double *u, double *w, double h1, do
             const float a = (float)h1, b = (float)h2;
             const dfp H1 = {a, (float)(h1 - (double)a)}, H2 = {b, (float)(h2 - (double)b)};
             const int v = sem_ax_variant(c->N, SEM_F64);
-            constexpr int N1 = dfeo_ne<NP>(1), N2 = dfeo_ne<NP>(2);
-            if (v == 1 && N1 != AxEoCfg<NP>::NE) return launch_dfeo<NP, N1>(c, u, w, H1, H2, s);
-            if (v == 2 && N2 != N1) return launch_dfeo<NP, N2>(c, u, w, H1, H2, s);
-            return launch_dfeo<NP, AxEoCfg<NP>::NE>(c, u, w, H1, H2, s);
+            constexpr int NE0 = AxEoCfg<NP>::NE, N2 = dfeo_ne<NP>(2), GS = dfeo_group_sync<NP>();
+            if (v == 1 && GS) return launch_dfeo<NP, NE0, GS>(c, u, w, H1, H2, s);
+            if (v == 2 && N2 != NE0) return launch_dfeo<NP, N2, 0>(c, u, w, H1, H2, s);
+            return launch_dfeo<NP, NE0, 0>(c, u, w, H1, H2, s);
         }
     }
     using C = AxDfCfg<NP>;

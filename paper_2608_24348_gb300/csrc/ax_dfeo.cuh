@@ -48,12 +48,29 @@ __host__ __device__ constexpr size_t ax_dfeo_smem_bytes()
 
 __device__ __forceinline__ dfp df_neg(dfp a) { return {-a.hi, -a.lo}; }
 
-// tab: the four half tables laid out [A | B | AT | BT], each H*H row-major [i][l].
-template <int NP, class Load, class Store>
+// Synchronisation between the stages of one element: GS == 0 is the block
+// barrier; GS > 0 is hardware barrier 1 + grp counted over the GS threads of
+// element group grp only (GS a multiple of 32; every thread of the group
+// reaches the same barriers), so the element groups of a block need not move
+// in step.
+template <int GS>
+__device__ __forceinline__ void dfeo_sync(int grp)
+{
+    if constexpr (GS == 0) {
+        __syncthreads();
+    } else {
+        static_assert(GS % 32 == 0, "a named barrier counts whole warps");
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "n"(GS) : "memory");
+    }
+}
+
+// tab: the four half tables laid out [A | B | AT | BT], each H*H row-major [i][l],
+// loaded and published before the first call.
+template <int NP, int GS = 0, class Load, class Store>
 __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &store,
                                                 const dfp *__restrict__ geo, dfp h1, dfp h2,
                                                 const dfp *__restrict__ tab, dfp *__restrict__ slab,
-                                                int *sexp, int tid, bool active)
+                                                int *sexp, int tid, bool active, int grp = 0)
 {
     constexpr int H = NP / 2, NP2 = NP * NP, NP3 = NP2 * NP, HH = H * H;
     constexpr int LS = AxEoCfg<NP>::LS, SL = AxEoCfg<NP>::SLAB;
@@ -63,7 +80,7 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
     // ---- load, element exponent, split
     double xu[NP];
     if (tid == 0) *sexp = 0;
-    __syncthreads();
+    dfeo_sync<GS>(grp);
     if (active) {
         int m = 0;
 #pragma unroll
@@ -73,7 +90,7 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
         }
         atomicMax(sexp, m);
     }
-    __syncthreads();
+    dfeo_sync<GS>(grp);
     const int E = *sexp > 0 ? *sexp - 1023 : 0;
     dfp ru[NP];
     if (active) {
@@ -83,7 +100,7 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
             su[(k * NP + j) * LS + i] = ru[k];
         }
     }
-    __syncthreads();
+    dfeo_sync<GS>(grp);
     // ---- fold the r-line (k = j, row i) into f1 and the s-line (k = j, column i) into f2
     if (active) {
         const dfp *lr = su + (j * NP + i) * LS;
@@ -101,7 +118,7 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
             f2[(j * NP + H + l) * LS + i] = df_sum(a, df_neg(b));
         }
     }
-    __syncthreads();
+    dfeo_sync<GS>(grp);
     // ---- gradient: r pairs -> g1, s pairs -> g2, t in registers
     dfp ut[NP];
     if (active) {
@@ -154,7 +171,7 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
             ut[NP - 1 - kp] = df_sum(bv, df_neg(av));
         }
     }
-    __syncthreads();
+    dfeo_sync<GS>(grp);
     // ---- geometric factors (column owner): vr -> f1, vs -> f2, vt in registers
     dfp rw[NP];
     if (active) {
@@ -176,7 +193,7 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
             rw[k] = df_raw(vw);
         }
     }
-    __syncthreads();
+    dfeo_sync<GS>(grp);
     // ---- fold vr (r-line k = j, row i) into g1, vs (s-line k = j, column i) into g2
     if (active) {
         const dfp *lr = f1 + (j * NP + i) * LS;
@@ -194,7 +211,7 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
             g2[(j * NP + H + l) * LS + i] = df_sum(a, df_neg(b));
         }
     }
-    __syncthreads();
+    dfeo_sync<GS>(grp);
     // ---- transpose: r pairs -> f1, s pairs -> f2, t in registers
     dfp wt[NP];
     if (active) {
@@ -247,7 +264,7 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
             wt[NP - 1 - kp] = df_sum(bv, df_neg(av));
         }
     }
-    __syncthreads();
+    dfeo_sync<GS>(grp);
     // ---- sum of the three directions, h1 / h2 weights, rounding to FP64
     if (active) {
 #pragma unroll
@@ -261,7 +278,7 @@ __device__ __forceinline__ void ax_dfeo_element(const Load &load, const Store &s
             store(p, df_join_scaled(df_raw(o), E));
         }
     }
-    __syncthreads();
+    dfeo_sync<GS>(grp);
 }
 
 // Host: the four half tables from the FP64 derivative matrix D (row-major n x n).
