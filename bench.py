@@ -42,7 +42,7 @@ FLOPS_PER_NODE = 12 * (N_ORDER + 1) + 21  # FP64 flops of one operator applicati
 # weights and split of the FP64 join
 # (profiles/sem_ax_dfeo_24cubed_N7.md measures about 434 FMA-pipe ops per node)
 DF_OPS_PER_NODE = 6 * 48 + 2 * 3 * 8 + (4 * 4 + 6 * 12) + (2 * 8 + 4 + 12) + 2
-DF_KERNEL = "k_ax_dfeo<8>"
+DF_KERNEL = "k_ax_dfeo<8,4,0>"
 # DRAM bytes per local node of k_ax_dfeo<8> (4 elements per block) from the ncu
 # capture on the 24^3 mesh (453.33 MB read + 48.27 MB written for 7,077,888
 # nodes), scaled to the 32^3 mesh
