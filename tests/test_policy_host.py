@@ -91,3 +91,109 @@ def test_peak_is_the_vertex_of_the_parabola_through_the_top_samples():
     assert abs(tp - 1.234) < 2e-3 and abs(yp - 1.0) < 1e-4
     # a maximum at the end of the record stays the last sample
     assert policy.peak(t, t) == (pytest.approx(1.9), pytest.approx(1.9))
+
+
+class _FakeEvent:
+    def __init__(self, enable_timing=False):
+        self.t = 0.0
+
+    def record(self, stream=None):
+        import time
+        self.t = time.perf_counter()
+
+    def elapsed_time(self, other):
+        return 1000.0 * (other.t - self.t)
+
+
+class _FakeStream:
+    def synchronize(self):
+        pass
+
+
+class _FakeCtx:
+    def __init__(self, N, nel, L, periodic):
+        self.nL = 8
+
+    def coords(self, xyz):
+        xyz.zero_()
+
+
+def _fake_tgv_class(histories):
+    """TGV stand-in whose KE / enstrophy follow histories[config](t)."""
+    class FakeTGV:
+        def __init__(self, ctx, nu, dt, op, vel, pres):
+            self.dt, self.n, self.cfg = dt, 0, None
+
+        def set_policy(self, rules):
+            self.cfg = [k for k, v in policy.TABLE2.items() if all(rules[0][b] == v[b] for b in v)][0]
+
+        def set_projection(self, n):
+            pass
+
+        def set(self, *fields):
+            pass
+
+        def energy(self):
+            return histories[self.cfg](0.0)[:2]
+
+        def step(self, n, stream=None):
+            out = []
+            for _ in range(n):
+                self.n += 1
+                t = self.n * self.dt
+                ke, en, status = histories[self.cfg](t)
+                out.append(dict(t=t, ke=ke, enstrophy=en, iters=[3, 2, 2, 2], status=status))
+            return out
+
+        def close(self):
+            pass
+    return FakeTGV
+
+
+def test_long_run_bookkeeping_without_a_gpu(monkeypatch):
+    """Chunked stepping, the stop conditions, the enstrophy peak, the dissipation
+    from the KE history and the errors against A-0, on a stepper stand-in with
+    closed-form histories."""
+    import math
+
+    import torch
+
+    def a0(t):  # KE decays at rate 2 nu Omega with Omega = 1 + exp(-(t-3)^2) (nu = 1/2)
+        ke = 0.125 - (t + math.sqrt(math.pi) / 2 * (math.erf(t - 3) + math.erf(3)))
+        return ke + 10.0, 1.0 + math.exp(-(t - 3) ** 2), 0
+
+    def a1(t):  # 1e-6 relative off A-0
+        ke, en, _ = a0(t)
+        return ke * (1 + 1e-6), en * (1 + 1e-6), 0
+
+    def b0(t):  # diverges at t = 2
+        ke, en, _ = a0(t)
+        return (float("nan"), en, 0) if t >= 2.0 else (ke, en, 0)
+
+    def b5(t):  # a solve fails at t = 1
+        ke, en, _ = a0(t)
+        return ke, en, (-4 if t >= 1.0 else 0)
+
+    monkeypatch.setattr(sem, "Ctx", _FakeCtx)
+    monkeypatch.setattr(sem, "TGV", _fake_tgv_class({"A-0": a0, "A-1": a1, "B-0": b0, "B-5": b5}))
+    monkeypatch.setattr(sem, "opts", lambda **kw: kw)
+    monkeypatch.setattr(torch.cuda, "Event", _FakeEvent)
+    monkeypatch.setattr(torch.cuda, "Stream", _FakeStream)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: __import__("contextlib").nullcontext())
+    real_empty = torch.empty
+    monkeypatch.setattr(torch, "empty", lambda *a, device=None, **kw: real_empty(*a, **kw))
+    rows = policy.long_run(["A-0", "A-1", "B-0", "B-5"], nel=2, N=3, re=2.0, dt=0.01, t_end=6.0,
+                           projection=4, chunk=70, every=50)
+    r = {row["config"]: row for row in rows}
+    assert r["A-0"]["steps"] == 600 and r["A-0"]["stopped"] is None
+    assert r["A-0"]["t_peak"] == pytest.approx(3.0, abs=1e-6)
+    assert r["A-0"]["enstrophy_peak"] == pytest.approx(2.0, abs=1e-5)
+    assert r["A-0"]["eps_peak"] == pytest.approx(2.0, abs=1e-5)          # 2 nu Omega, nu = 1/2
+    assert r["A-0"]["eps_ke_at_peak"] == pytest.approx(2.0, rel=1e-3)    # -dKE/dt of the history
+    assert len(r["A-0"]["series"]) == 12 and r["A-0"]["series"][0][0] == pytest.approx(0.5)
+    assert r["A-0"]["e_E_max"] == 0.0 and r["A-1"]["e_Omega_max"] == pytest.approx(1e-6, rel=1e-3)
+    # B-0 stops in the chunk where KE turned non-finite, B-5 in the one with the failed solve
+    assert r["B-0"]["stopped"] == "non-finite KE or enstrophy" and 200 <= r["B-0"]["steps"] < 270
+    assert r["B-5"]["stopped"] == "solve status -4" and 100 <= r["B-5"]["steps"] < 170
+    assert r["B-5"]["e_Omega_max"] == 0.0  # errors over the steps both runs reached
+    assert "ke" not in r["A-0"] and all(row["pres_iters"] == 3.0 for row in rows)
