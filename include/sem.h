@@ -260,13 +260,20 @@ typedef struct {
     int status;
 } sem_tgv_diag;
 
-/* Stepper on a periodic context (N <= 9).  nu: viscosity; dt: time step.
+/* Stepper on a periodic context (Sec. 3: the P_N-P_N splitting with BDF3/EXT3
+ * and 3/2-rule dealiasing; N <= 9).  nu: viscosity; dt: time step (fixed).
  * op: precision of the dealiased convection: SEM_F64 (FP64-accurate, float
  * pairs on the FP32 pipes), SEM_F64_NATIVE (FP64 arithmetic) or SEM_F32
  * (histories, right-hand sides, refinement residuals and diagnostics stay FP64).  vel / pres: options
  * of the velocity Helmholtz and pressure Poisson solves (NULL = defaults: FP64
  * PCG; with op = SEM_F32 the default pressure solve is an FP32 inner PCG inside
- * FP64 refinement).  The solves' inner field selects their precision. */
+ * FP64 refinement).  The solves' inner field selects their precision.
+ * The stepper keeps a reference to ctx (which must outlive it) and solves on
+ * the context's workspace slots 4-7; it allocates about 32 FP64 E-vectors plus
+ * J^-1 and float-pair tables on the device (SEM_ERR_NOMEM if they do not fit).
+ * SEM_ERR_ARG: NULL ctx or out, nu or dt not positive, an unsupported op, a
+ * context that is not periodic in all three directions, or N > 9.  The state
+ * is zero until sem_tgv_set. */
 SEM_API int sem_tgv_init(sem_ctx *ctx, double nu, double dt, sem_dtype op, const sem_solve_opts *vel,
                  const sem_solve_opts *pres, sem_tgv **out);
 
@@ -316,22 +323,39 @@ SEM_API int sem_tgv_set_policy(sem_tgv *tgv, int n, const sem_tgv_policy *rules)
 SEM_API int sem_tgv_set_projection(sem_tgv *tgv, int max_vectors);
 
 /* Set the state at history level (0 = u^n, 1 = u^{n-1}, 2 = u^{n-2}) from
- * FP64 E-vectors u, v, w (and p for level 0; may be NULL); step is the number
- * of steps already taken (selects the startup order), t the time. */
+ * FP64 E-vectors u, v, w (and p for level 0; may be NULL), each device or host
+ * memory (copied); step is the number of steps already taken (selects the
+ * startup order: 0 = first order next), t the time.  Levels 1 and 2 also
+ * evaluate that level's convective term.  Synchronises the stream.
+ * SEM_ERR_ARG: NULL tgv, u, v or w, level outside 0..2, or step < 0. */
 SEM_API int sem_tgv_set(sem_tgv *tgv, int level, const double *u, const double *v, const double *w,
                 const double *p, int step, double t, void *stream);
 
 /* Advance nsteps P_N-P_N steps (BDF3/EXT3, 3/2-rule dealiasing).  diag: host
  * array of nsteps entries or NULL; when given, the call synchronises (after
- * every 4096 steps at most: the device keeps a ring of 4096 log entries). */
+ * every 4096 steps at most: the device keeps a ring of 4096 log entries) and
+ * returns the first nonzero solve status of those steps
+ * (SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN or SEM_ERR_TIMEOUT; the steps still
+ * ran, with the last iterate of that solve); without diag the call is
+ * stream-ordered and returns SEM_OK or a launch error.  From the third step on
+ * each step is one CUDA graph replay (captured on the second steady step after
+ * setup or any policy or projection change; direct launches if the capture
+ * fails) when stream is not NULL.
+ * SEM_ERR_ARG: NULL tgv or nsteps < 0. */
 SEM_API int sem_tgv_step(sem_tgv *tgv, int nsteps, sem_tgv_diag *diag, void *stream);
 
-/* Copy out u^n, v^n, w^n, p^n (FP64 E-vectors; any may be NULL). */
+/* Copy out u^n, v^n, w^n, p^n (FP64 E-vectors, device or host memory; any
+ * may be NULL); stream-ordered (a host destination is valid after a stream
+ * synchronisation).  SEM_ERR_ARG: NULL tgv. */
 SEM_API int sem_tgv_get(sem_tgv *tgv, double *u, double *v, double *w, double *p, void *stream);
 
-/* Kinetic energy and enstrophy of the current state (host doubles). */
+/* Kinetic energy and enstrophy of the current state (Sec. 4.2 diagnostics;
+ * host doubles, FP64-accurate reductions); synchronises the stream.  SEM_ERR_ARG: a
+ * NULL argument. */
 SEM_API int sem_tgv_energy(sem_tgv *tgv, double *ke, double *enstrophy, void *stream);
 
+/* Free a stepper (NULL is allowed); synchronises the device first.  The
+ * context stays valid. */
 SEM_API void sem_tgv_destroy(sem_tgv *tgv);
 
 #ifdef __cplusplus
