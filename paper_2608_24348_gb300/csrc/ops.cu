@@ -122,7 +122,7 @@ static AxPipe *ax_pipe(sem_ctx *c)
              cudaEventCreateWithFlags(&P->ev_cmp[k], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
-        free(P);  // (handles created before the failure are left to the driver's teardown)
+        free(P);  // (handles created before the failure are left to the CUDA driver's teardown at exit)
         return nullptr;
     }
     c->pipe = P;
