@@ -97,13 +97,14 @@ void sem_pipe_destroy(void *pipe)
 {
     AxPipe *P = (AxPipe *)pipe;
     if (!P) return;
-    cudaStreamDestroy(P->in);
-    cudaStreamDestroy(P->out);
-    cudaEventDestroy(P->start);
-    cudaEventDestroy(P->done);
+    // handles that were never created are null (the struct is zero-initialised)
+    if (P->in) cudaStreamDestroy(P->in);
+    if (P->out) cudaStreamDestroy(P->out);
+    if (P->start) cudaEventDestroy(P->start);
+    if (P->done) cudaEventDestroy(P->done);
     for (int k = 0; k < SEM_PIPE_CHUNKS; ++k) {
-        cudaEventDestroy(P->ev_in[k]);
-        cudaEventDestroy(P->ev_cmp[k]);
+        if (P->ev_in[k]) cudaEventDestroy(P->ev_in[k]);
+        if (P->ev_cmp[k]) cudaEventDestroy(P->ev_cmp[k]);
     }
     free(P);
 }
@@ -122,7 +123,7 @@ static AxPipe *ax_pipe(sem_ctx *c)
              cudaEventCreateWithFlags(&P->ev_cmp[k], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
-        free(P);  // (handles created before the failure are left to the CUDA driver's teardown at exit)
+        sem_pipe_destroy(P);
         return nullptr;
     }
     c->pipe = P;
