@@ -37,3 +37,26 @@ def test_strerror_without_gpu():
     L = sem.load()
     assert L.sem_strerror(-5).decode() == "solver did not converge"
     assert L.sem_strerror(0).decode() == "ok"
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the CUDA library absent, load() raises."""
+    import pytest
+
+    from paper_2608_24348_gb300 import sem
+    monkeypatch.setattr(sem, "_lib", None)
+    monkeypatch.setattr(sem._build, "LIB", str(tmp_path / "libsem.so"))
+    with pytest.raises(RuntimeError, match="CUDA extension is required"):
+        sem.load(build_if_missing=False)
+
+
+def test_package_never_imports_the_oracle():
+    """The product package reaches no code under oracle/ (the oracle is test
+    infrastructure only)."""
+    pkg = os.path.join(ROOT, "paper_2608_24348_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c")):
+                txt = open(os.path.join(dirpath, f), errors="replace").read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, re.M), f
+                assert "sem_oracle" not in txt and "liboracle" not in txt, f
