@@ -197,3 +197,42 @@ def test_long_run_bookkeeping_without_a_gpu(monkeypatch):
     assert r["B-5"]["stopped"] == "solve status -4" and 100 <= r["B-5"]["steps"] < 170
     assert r["B-5"]["e_Omega_max"] == 0.0  # errors over the steps both runs reached
     assert "ke" not in r["A-0"] and all(row["pres_iters"] == 3.0 for row in rows)
+
+
+def test_replay_bookkeeping_without_a_gpu(monkeypatch):
+    """Table 2 replay on a stepper stand-in: A-0 is prepended as the reference,
+    the timed steps exclude the start-up ones, iteration means and the worst
+    status are reported, and a configuration whose start-up solve fails keeps
+    only those steps and no timing."""
+    import math
+
+    import torch
+
+    def a0(t):
+        return 0.125 * math.exp(-t), 0.375 * (1 + t), 0
+
+    def a4(t):
+        ke, en, _ = a0(t)
+        return ke * (1 + 2e-7), en * (1 - 3e-7), 0
+
+    def b7(t):  # the second start-up step fails to converge
+        ke, en, _ = a0(t)
+        return ke, en, (-5 if t >= 0.02 - 1e-12 else 0)
+
+    monkeypatch.setattr(sem, "Ctx", _FakeCtx)
+    monkeypatch.setattr(sem, "TGV", _fake_tgv_class({"A-0": a0, "A-4": a4, "B-7": b7}))
+    monkeypatch.setattr(sem, "opts", lambda **kw: kw)
+    monkeypatch.setattr(torch.cuda, "Event", _FakeEvent)
+    monkeypatch.setattr(torch.cuda, "Stream", _FakeStream)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: __import__("contextlib").nullcontext())
+    real_empty = torch.empty
+    monkeypatch.setattr(torch, "empty", lambda *a, device=None, **kw: real_empty(*a, **kw))
+    rows = policy.replay(["A-4", "B-7"], nel=2, N=3, dt=0.01, steps=40, warm=3, projection=4)
+    r = {row["config"]: row for row in rows}
+    assert [row["config"] for row in rows] == ["A-0", "A-4", "B-7"]
+    assert r["A-0"]["steps"] == 40 and r["A-0"]["ms_per_step"] >= 0 and r["A-0"]["status"] == 0
+    assert r["A-0"]["pres_iters"] == 3.0 and r["A-0"]["vel_iters"] == 2.0
+    assert r["A-4"]["e_E_max"] == pytest.approx(2e-7, rel=1e-3)
+    assert r["A-4"]["e_Omega_max"] == pytest.approx(3e-7, rel=1e-3)
+    assert r["B-7"]["steps"] == 3 and r["B-7"]["status"] == -5 and math.isnan(r["B-7"]["ms_per_step"])
+    assert r["B-7"]["e_E_max"] == 0.0
