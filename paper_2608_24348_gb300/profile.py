@@ -6,11 +6,59 @@ Kernels: ax_f64, ax_f32, ax_bf16_tc, dssum, pcg_f64, pcg_f32 (a bounded number
 of PCG iterations), tgv_f64, tgv_f32 (steps of the Taylor-Green stepper).
 The mesh is the benchmark's: nel^3 elements, order N, interior vertices
 perturbed by up to 10%.
+
+--kernel link times the host link instead (no library call): copies of one
+FP64 E-vector of the nel^3, order-N mesh between pinned host memory and the
+device, host-to-device alone, device-to-host alone and both at once on two
+streams, in GB/s per direction (the ceiling of the end-to-end sem_ax figure).
 """
 from __future__ import annotations
 
 import argparse
 import math
+
+
+def link_bandwidth(n, reps):
+    """GB/s per direction of n-double copies between pinned host memory and
+    cuda:0: host-to-device, device-to-host, and both concurrently."""
+    import torch
+    dev = torch.device("cuda:0")
+    a_h = torch.ones(n, dtype=torch.float64).pin_memory()
+    b_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    a_d = torch.empty(n, dtype=torch.float64, device=dev)
+    b_d = torch.ones(n, dtype=torch.float64, device=dev)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def h2d():
+        a_d.copy_(a_h, non_blocking=True)
+
+    def d2h():
+        b_h.copy_(b_d, non_blocking=True)
+
+    def both():
+        cur = torch.cuda.current_stream()
+        s1.wait_stream(cur)
+        s2.wait_stream(cur)
+        with torch.cuda.stream(s1):
+            a_d.copy_(a_h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            b_h.copy_(b_d, non_blocking=True)
+        cur.wait_stream(s1)
+        cur.wait_stream(s2)
+
+    out = {"bytes_per_direction": 8 * n}
+    for name, fn in (("h2d", h2d), ("d2h", d2h), ("both", both)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "GBps_per_direction": 8 * n / ms / 1e6}
+    return out
 
 
 def main(argv=None):
@@ -30,6 +78,9 @@ def main(argv=None):
 
     from . import inputs, sem
     dev = torch.device("cuda:0")
+    if args.kernel == "link":
+        print(json.dumps(link_bandwidth(args.nel ** 3 * (args.N + 1) ** 3, max(args.reps, 3))))
+        return
     nel = (args.nel,) * 3
     tgv = args.kernel.startswith("tgv")
     v = inputs.box_vertices(nel, (2 * math.pi,) * 3, perturb=0.0 if tgv else 0.1)
