@@ -283,6 +283,52 @@ def test_dssum_is_QQt_and_multiplicity(N, periodic):
     np.testing.assert_allclose(m.dssum(uc / m.mult), uc, rtol=1e-14)
 
 
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 0, 0), (1, 0, 1)])
+@pytest.mark.parametrize("N", [1, 3, 6])
+def test_glsc3_with_inverse_multiplicity_is_the_assembled_product(N, periodic):
+    """<a, b> = sum_local a b / mult equals sum over unique nodes a_g b_g for
+    continuous fields (the solver's norm, Sec. 2 glsc3).  The unique values
+    and their multiplicities come from the index layout here, not from the
+    oracle's dssum, so a dropped, inverted or squared weight fails."""
+    nel = (3, 2, 2)
+    m = mesh(N, nel, 0.1, periodic=periodic)
+    g = inputs.local_to_unique(N, nel, periodic)
+    ng = int(np.prod(inputs.unique_counts(N, nel, periodic)))
+    ag = np.random.default_rng(11).uniform(-1, 1, ng)
+    bg = np.random.default_rng(12).uniform(-1, 1, ng)
+    a, b = ag[g], bg[g]
+    exact = float(ag @ bg)
+    assert abs(m.glsc3(a, b) - exact) <= 1e-14 * np.abs(ag * bg).sum()
+    # the weights themselves: 1 / (number of local copies of each unique node)
+    counts = np.bincount(g, minlength=ng).astype(np.float64)
+    np.testing.assert_array_equal(m.imult, 1.0 / counts[g])
+    # explicit weights: a plain triple product
+    c = np.random.default_rng(13).uniform(0.5, 2.0, m.nL)
+    assert abs(m.glsc3(a, b, c) - float(np.sum(a * b * c))) <= 1e-14 * np.abs(a * b * c).sum()
+    # the norm of the constant is the square root of the unique-node count
+    one = np.ones(m.nL)
+    assert abs(m.glsc3(one, one) - ng) <= 1e-12 * ng
+
+
+@pytest.mark.parametrize("k", [(1, 0, 0), (0, -3, 2), (2, 5, -1)])
+def test_fourier_single_modes_match_numpy(k):
+    """One mode k with coefficients (cc, cs): cc cos(k.x) + cs sin(k.x), evaluated
+    with numpy's cos/sin directly; two modes add."""
+    rng = np.random.default_rng(7)
+    x, y, z = (rng.uniform(-7, 7, 500) for _ in range(3))
+    K = np.array([k], dtype=np.int64)
+    ph = k[0] * x + k[1] * y + k[2] * z
+    np.testing.assert_allclose(oracle.fourier(K, [0.7], [0.0], x, y, z), 0.7 * np.cos(ph),
+                               rtol=0, atol=1e-13)
+    np.testing.assert_allclose(oracle.fourier(K, [0.0], [-1.3], x, y, z), -1.3 * np.sin(ph),
+                               rtol=0, atol=1e-13)
+    K2 = np.array([k, (1, 1, 1)], dtype=np.int64)
+    ph2 = x + y + z
+    np.testing.assert_allclose(oracle.fourier(K2, [0.5, 0.25], [0.0, 2.0], x, y, z),
+                               0.5 * np.cos(ph) + 0.25 * np.cos(ph2) + 2.0 * np.sin(ph2),
+                               rtol=0, atol=1e-12)
+
+
 def test_jacobi_equals_assembled_diagonal():
     N, nel, h1, h2 = 3, (2, 2, 2), 0.8, 3.0
     m = mesh(N, nel, 0.12)
