@@ -365,18 +365,18 @@ def main():
     line = {
         "metric": METRIC, "value": gdof(ms64), "unit": "GDOF/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "df64", "data": "synthetic",
         "config": {"workload": "sem_ax FP64 (FP64-accurate, FP32 pipes), 32^3 elements N=7 "
                                "deformed (16.8M local nodes), h1=0.01 h2=1000", "N": N_ORDER,
                    "elements": list(NEL), "local_nodes": nL,
                    "l2": "inputs larger than L2 (1.2 GB per application), no flush"},
-        "roofline": {"bound": "alu", "achieved": df_ops, "peak": fp32_peak, "unit": "Tops/s",
-                     "frac": df_ops / fp32_peak, "traffic": DF_TRAFFIC_PER_NODE * nL,
-                     "peak_src": "128 FP32-pipe ops/clk/SM x SMs x max SM clock",
-                     "kernel": DF_KERNEL, "ops_per_node": DF_OPS_PER_NODE,
-                     "hbm_achieved_gbs": hbm(BYTES_F64, avg64),
-                     "hbm_frac": hbm(BYTES_F64, avg64) / pk["hbm_gbs"],
-                     "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_src": pk["src"]},
+        "roofline": {"bound": "hbm", "achieved": hbm(BYTES_F64, avg64), "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": hbm(BYTES_F64, avg64) / pk["hbm_gbs"],
+                     "traffic": DF_TRAFFIC_PER_NODE * nL, "peak_src": pk["src"],
+                     "kernel": DF_KERNEL, "bytes_per_node": BYTES_F64,
+                     "alu": {"achieved": df_ops, "peak": fp32_peak, "unit": "Tops/s",
+                             "frac": df_ops / fp32_peak, "ops_per_node": DF_OPS_PER_NODE,
+                             "peak_src": "128 FP32-pipe ops/clk/SM x SMs x max SM clock"}},
         "native_f64": {"gdofs": gdof(barrier_max(tot_nat, ws) / k2),
                        "roofline": {"bound": "alu", "unit": "TFLOP/s",
                                     "achieved": FLOPS_PER_NODE * nL / (avg_nat * 1e-3) / 1e12,

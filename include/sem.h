@@ -228,25 +228,29 @@ SEM_API int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const double 
 
 /* FP64 Jacobi-PCG that allocates nothing -- an addition of this library; the
  * paper has no counterpart.  It is meant for callers that cannot call
- * cudaMalloc: code running while a stream is captured into a CUDA graph, code
- * whose device memory is owned by another allocator (a framework's caching
- * allocator, a plugin host, a service with a fixed memory plan), and code that
- * must avoid cudaMalloc's implicit device synchronisation.  It needs no
- * context: the caller passes the mesh shape (N, nelx, nely, nelz, periodic),
- * the geometric factors geom as a device FP64 array laid out element by
- * element, [E][7][(N+1)^3] with components G11 G22 G33 G12 G13 G23 B (the
- * factors sem_geom exports, regrouped per element), the assembled RHS b and
- * the initial guess / solution x (device FP64 E-vectors), and host opts/info
- * (info is required; opts->inner must be SEM_F64).  The arithmetic is that of
- * sem_pcg_solve (same persistent kernel).  Every scratch vector, partial sum
- * and the solver state live in one file-scope device array of fixed size
- * (about 33 MB, held on every GPU that loads the library until the process
- * exits), so problems with more than SEM_NOALLOC_MAX_NODES local nodes return
- * SEM_ERR_TOO_LARGE.  The first call on a device looks up that array's device
- * address (once per device); make that first call before any stream capture
- * begins.  All calls share the one array: calls that overlap on the GPU (from
- * several streams or host threads) race and give wrong results.  The call
- * synchronises the stream and returns info->status. */
+ * cudaMalloc: code whose device memory is owned by another allocator (a
+ * framework's caching allocator, a plugin host, a service with a fixed memory
+ * plan), and code that must avoid cudaMalloc's implicit device
+ * synchronisation.  It needs no context: the caller passes the mesh shape (N,
+ * nelx, nely, nelz, periodic), the geometric factors geom as a device FP64
+ * array laid out element by element, [E][7][(N+1)^3] with components G11 G22
+ * G33 G12 G13 G23 B (the factors sem_geom exports, regrouped per element), the
+ * assembled RHS b and the initial guess / solution x (device FP64 E-vectors),
+ * and host opts/info (info is required; opts->inner must be SEM_F64 or
+ * SEM_F64_NATIVE, and either runs the native-FP64 operator: the arithmetic of
+ * sem_pcg_solve with inner = SEM_F64_NATIVE, same persistent kernel).  Every
+ * scratch vector, partial sum and the solver state live in one file-scope
+ * device array of fixed size (about 33 MB, held on every GPU that loads the
+ * library until the process exits), so problems with more than
+ * SEM_NOALLOC_MAX_NODES local nodes return SEM_ERR_TOO_LARGE.  The first call
+ * on a device looks up that array's device address (once per device, cached
+ * for the process; a cudaDeviceReset of that device makes the cached address
+ * stale, so calls after a reset are not supported).  All calls share the one
+ * array, which keeps the previous call's contents (the call clears the solver
+ * state itself): calls that overlap on the GPU (from several streams or host
+ * threads) race and give wrong results.  The call reads the mesh volume back
+ * to the host, synchronises the stream before returning and returns
+ * info->status. */
 SEM_API int sem_pcg_solve_noalloc(int N, int nelx, int nely, int nelz, const int periodic[3],
                                   const double *geom, const double *b, double *x, double h1,
                                   double h2, const sem_solve_opts *opts, sem_solve_info *info,

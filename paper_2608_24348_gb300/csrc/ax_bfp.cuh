@@ -1,0 +1,397 @@
+// ax_bfp.cuh -- FP64-accurate element operator on the FP32 pipes with
+// block-floating-point pairs.
+//
+// Every value of one element's stage is a pair (X, x) of FP32 numbers whose
+// sum is the value: X is a multiple of a per-element power-of-two quantum q
+// with |X| <= 2^22 q (a 23-bit fixed-point number stored in a float), x is an
+// ordinary float that holds what X cannot (|x| of order q).  Two properties
+// make the arithmetic cheap:
+//   - X_a +- X_b is exact (|result| <= 2^23 q < 2^24 q), so the even-odd fold
+//     of a line (the GLL derivative matrix is centro-antisymmetric,
+//     D[N-i][N-l] = -D[i][l]) costs two plain adds per pair;
+//   - a sum of products accumulates in t = C + sum, with C = 1.5 * 2^23 * q':
+//     while |sum| < 2^22 q', t stays in the binade [2^23 q', 2^24 q') whose
+//     spacing is q', so tn = fma(a, b, t) rounds a*b + t to the grid, t - tn
+//     is exact and fma(a, b, t - tn) is that rounding error (up to the float
+//     rounding of a quantity of size q').  Four operations per product give
+//     the grid part and its remainder (fast two-sum with the magnitude order
+//     known in advance, fused with Dekker's exact product); the cross terms
+//     a_hi b_lo + a_lo b_hi add two more.
+// The quantum of each sum follows from a bound on its partial sums, as tight
+// as is cheap: the gradient stage uses a constant per output row (|u 2^-E| < 1
+// times the row sums of the half tables; the boundary row of D sums to ~6x
+// the interior rows); the geometric stage bounds each node by its own factors
+// and gradients (the GLL weights make G vary ~10^3-fold inside an element);
+// the transpose stage re-quantises each line to its own largest value before
+// folding and bounds it by that value.  The last stage (the three directions,
+// the h1, h2 weights) uses two-sums and Dekker products, so it needs no
+// bound, and joins the pair into FP64 with the element scale 2^E applied to
+// the exponent field.  The result is accurate to a few 2^-44 of each stage's
+// largest value, inside the FP64 operator's 1e-12 bar; the parity tests
+// measure it.
+//
+// Thread (i, j) of an element owns column u[.][j][i] (the t direction in
+// registers), the r line (j' = i, k' = j) and the s line (i' = i, k' = j);
+// line data moves through three padded shared-memory slabs of pairs.
+#pragma once
+
+#include "ax_df.cuh"
+#include "common.cuh"
+
+template <int NP>
+struct BfpCfg {
+    static constexpr int H = NP / 2;
+    static constexpr int NP2 = NP * NP, NP3 = NP2 * NP;
+    static constexpr int NE = (256 / NP2) > 0 ? (256 / NP2) : 1;
+    static constexpr int THREADS = NE * NP2;
+    static constexpr bool OK = (NP % 2) == 0;
+    static constexpr int LS = NP + 1;        // padded line stride of a slab (pairs)
+    static constexpr int SLAB = NP2 * LS;    // pairs per slab
+    static constexpr bool WHOLE_WARPS = (NP2 % 32) == 0;
+    static constexpr int WPE = WHOLE_WARPS ? NP2 / 32 : 1;  // warps per element
+};
+
+// Folded half tables of D (index 0, gradient) and D^T (index 1), hi and lo
+// parts: A_il = (M_il + M_{i,N-l})/2, B_il = (M_il - M_{i,N-l})/2 for l < H.
+// Passed by value as a kernel parameter: the unrolled loops index it with
+// constants, so every table entry is a constant-bank operand.
+struct BfpTabs {
+    float ah[2][SEM_NPMAX / 2][SEM_NPMAX / 2], al[2][SEM_NPMAX / 2][SEM_NPMAX / 2];
+    float bh[2][SEM_NPMAX / 2][SEM_NPMAX / 2], bl[2][SEM_NPMAX / 2][SEM_NPMAX / 2];
+    float cm_grad[SEM_NPMAX / 2];  // gradient stage: accumulator offset of output row i (|X| <= 1)
+    float kt;       // transpose stage: bound of its partial sums per unit of the line's largest input
+};
+
+// Shared memory: per element three slabs and 8 reduction words.
+template <int NP, int NE>
+__host__ __device__ constexpr size_t ax_bfp_smem_bytes_ne()
+{
+    return sizeof(dfp) * (size_t)NE * 3 * BfpCfg<NP>::SLAB + sizeof(unsigned) * 8 * (size_t)NE;
+}
+
+// Accumulator offset C = 1.5 * 2^23 * q for a bound B of the partial sums,
+// with q = 2^(e_B + 1 - 22) >= B / 2^22 (e_B the exponent of B).
+__device__ __forceinline__ float bfp_offset(float B)
+{
+    unsigned e = __float_as_uint(B) & 0x7f800000u;
+    if (e > 0x7d000000u) e = 0x7d000000u;
+    return __uint_as_float((e + 0x01000000u) | 0x00400000u);
+}
+
+// One product term a * x added to the accumulator (t on the grid, lo the rest).
+__device__ __forceinline__ void bfp_term(float &t, float &lo, float ah, float al, float xh, float xl)
+{
+    const float tn = __fmaf_rn(ah, xh, t);
+    const float d = __fsub_rn(t, tn);
+    lo = __fadd_rn(lo, __fmaf_rn(ah, xh, d));
+    lo = __fmaf_rn(ah, xl, lo);
+    lo = __fmaf_rn(al, xh, lo);
+    t = tn;
+}
+
+// The first term of a sum: t starts at the offset C.
+__device__ __forceinline__ void bfp_first(float &t, float &lo, float C, float ah, float al, float xh,
+                                          float xl)
+{
+    t = __fmaf_rn(ah, xh, C);
+    lo = __fmaf_rn(ah, xh, __fsub_rn(C, t));
+    lo = __fmaf_rn(ah, xl, lo);
+    lo = __fmaf_rn(al, xh, lo);
+}
+
+// y = M x along one line (M = D for DIR 0, D^T for DIR 1).  x: grid parts on a
+// common quantum with |X| <= 2^22 q_in.  off(i): the accumulator offset of
+// output rows i and N-i.  y: grid parts on that quantum (|Y| <= 2^23 q),
+// remainders in lo.
+template <int NP, int DIR, class Off>
+__device__ __forceinline__ void bfp_line(const dfp (&x)[NP], dfp (&y)[NP], const Off &off,
+                                         const BfpTabs &T)
+{
+    constexpr int H = NP / 2;
+    float eh[H], el[H], oh[H], ol[H];
+#pragma unroll
+    for (int l = 0; l < H; ++l) {
+        eh[l] = __fadd_rn(x[l].hi, x[NP - 1 - l].hi);
+        oh[l] = __fsub_rn(x[l].hi, x[NP - 1 - l].hi);
+        el[l] = __fadd_rn(x[l].lo, x[NP - 1 - l].lo);
+        ol[l] = __fsub_rn(x[l].lo, x[NP - 1 - l].lo);
+    }
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const float C = off(i), C2 = __fadd_rn(C, C);
+        float ta, la, tb, lb;
+        bfp_first(ta, la, C, T.ah[DIR][i][0], T.al[DIR][i][0], eh[0], el[0]);
+        bfp_first(tb, lb, C, T.bh[DIR][i][0], T.bl[DIR][i][0], oh[0], ol[0]);
+#pragma unroll
+        for (int l = 1; l < H; ++l) {
+            bfp_term(ta, la, T.ah[DIR][i][l], T.al[DIR][i][l], eh[l], el[l]);
+            bfp_term(tb, lb, T.bh[DIR][i][l], T.bl[DIR][i][l], oh[l], ol[l]);
+        }
+        // ta = C + a, tb = C + b:  y_i = a + b,  y_{N-i} = b - a (all exact on the grid)
+        y[i].hi = __fadd_rn(ta, __fsub_rn(tb, C2));
+        y[i].lo = __fadd_rn(la, lb);
+        y[NP - 1 - i].hi = __fsub_rn(tb, ta);
+        y[NP - 1 - i].lo = __fsub_rn(lb, la);
+    }
+}
+
+// Largest value of m over one element's threads; slot: NE x 8 words.  The
+// result is valid after the next barrier (read with bfp_group_max_read).
+template <int NP>
+__device__ __forceinline__ void bfp_group_max_write(unsigned m, unsigned *slot, int tid)
+{
+    using C = BfpCfg<NP>;
+    if constexpr (C::WHOLE_WARPS) {
+        const unsigned r = __reduce_max_sync(0xffffffffu, m);
+        if ((tid & 31) == 0) slot[tid >> 5] = r;
+    } else {
+        atomicMax(slot, m);
+    }
+}
+
+template <int NP>
+__device__ __forceinline__ unsigned bfp_group_max_read(const unsigned *slot)
+{
+    using C = BfpCfg<NP>;
+    unsigned m = slot[0];
+    if constexpr (C::WHOLE_WARPS) {
+#pragma unroll
+        for (int w = 1; w < C::WPE; ++w) m = max(m, slot[w]);
+    }
+    return m;
+}
+
+// Clears the slot for the atomic form (before the barrier that precedes its writers).
+template <int NP>
+__device__ __forceinline__ void bfp_group_max_clear(unsigned *slot, int tid)
+{
+    if constexpr (!BfpCfg<NP>::WHOLE_WARPS) {
+        if (tid == 0) *slot = 0u;
+    }
+}
+
+// Re-quantises a line to the grid of its largest grid part M (|X| <= 2^22 q
+// after it) and returns M.  The rounding remainders join the lo parts.
+template <int NP>
+__device__ __forceinline__ float bfp_requantise(dfp (&x)[NP])
+{
+    float M = fabsf(x[0].hi);
+#pragma unroll
+    for (int l = 1; l < NP; ++l) M = fmaxf(M, fabsf(x[l].hi));
+    const float Cs = bfp_offset(M);
+#pragma unroll
+    for (int l = 0; l < NP; ++l) {
+        const float X = __fsub_rn(__fadd_rn(x[l].hi, Cs), Cs);
+        x[l].lo = __fadd_rn(x[l].lo, __fsub_rn(x[l].hi, X));
+        x[l].hi = X;
+    }
+    return M;
+}
+
+// a + b for floats, the rounding error added to err (Knuth's two-sum).
+__device__ __forceinline__ float bfp_two_sum(float a, float b, float &err)
+{
+    const float s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    err = __fadd_rn(err, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv)));
+    return s;
+}
+
+// One element.  load(p) -> double (u at local node p), store(p, double).
+// geo: the element's float-pair factors [7][NP^3].  slab: 3 slabs; red: 8
+// words (the exponent reduction).  All threads of the block call it (barriers
+// are block-wide).
+template <int NP, class Load, class Store>
+__device__ __forceinline__ void ax_bfp_element(const Load &load, const Store &store,
+                                               const dfp *__restrict__ geo, dfp h1, dfp h2,
+                                               const BfpTabs &T, dfp *__restrict__ slab,
+                                               unsigned *red, int tid, bool active)
+{
+    using Cf = BfpCfg<NP>;
+    constexpr int NP2 = Cf::NP2, NP3 = Cf::NP3, LS = Cf::LS, SL = Cf::SLAB;
+    dfp *su = slab, *sA = slab + SL, *sB = sA + SL;
+    const int i = tid % NP, j = tid / NP;
+
+    // ---- load, element exponent
+    double xu[NP];
+    unsigned m = 0;
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            xu[k] = load(k * NP2 + tid);
+            m = max(m, (unsigned)df_bexp(xu[k]));
+        }
+    }
+    bfp_group_max_write<NP>(m, red, tid);
+    __syncthreads();
+    const unsigned bmax = bfp_group_max_read<NP>(red);
+    // u 2^-E has |.| < 1
+    const int E = bmax > 0 ? (int)bmax - 1022 : 0;
+    dfp ru[NP];
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            dfp s = df_split_scaled(xu[k], E);
+            // grid part on the quantum 2^-22 (offset 3 = 1.5 * 2^23 * 2^-22)
+            const float X = __fsub_rn(__fadd_rn(s.hi, 3.0f), 3.0f);
+            ru[k] = {X, __fadd_rn(s.lo, __fsub_rn(s.hi, X))};
+            su[(k * NP + j) * LS + i] = ru[k];
+        }
+    }
+    __syncthreads();
+    // the atomic form of the reduction starts the next element from zero
+    bfp_group_max_clear<NP>(red, tid);
+
+    // ---- gradient: r line (j' = i, k' = j) -> sA, s line (i' = i, k' = j) -> sB, t in registers
+    dfp gt[NP];
+    if (active) {
+        auto off = [&](int r) { return T.cm_grad[r]; };
+        {
+            dfp x[NP], y[NP];
+            const dfp *lr = su + (j * NP + i) * LS;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) x[l] = lr[l];
+            bfp_line<NP, 0>(x, y, off, T);
+            dfp *or_ = sA + (j * NP + i) * LS;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) or_[l] = y[l];
+        }
+        {
+            dfp x[NP], y[NP];
+#pragma unroll
+            for (int l = 0; l < NP; ++l) x[l] = su[(j * NP + l) * LS + i];
+            bfp_line<NP, 0>(x, y, off, T);
+#pragma unroll
+            for (int l = 0; l < NP; ++l) sB[(j * NP + l) * LS + i] = y[l];
+        }
+        bfp_line<NP, 0>(ru, gt, off, T);
+    }
+    __syncthreads();
+
+    // ---- geometric factors (column owner): v_a = sum_b G_ab g_b, each node on
+    // its own quantum; h2 B u as a Dekker pair for the last stage
+    dfp bu[NP];
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int p = k * NP2 + tid, q = (k * NP + j) * LS + i;
+            const dfp gr = sA[q], gs = sB[q], gq = gt[k];
+            const dfp g11 = geo[0 * NP3 + p], g22 = geo[1 * NP3 + p], g33 = geo[2 * NP3 + p];
+            const dfp g12 = geo[3 * NP3 + p], g13 = geo[4 * NP3 + p], g23 = geo[5 * NP3 + p];
+            const dfp bm = geo[6 * NP3 + p];
+            // bound: max_a sum_b |G_ab| times max_b |g_b| (grid parts), with margin
+            const float rs = fmaxf(fabsf(g11.hi) + fabsf(g12.hi) + fabsf(g13.hi),
+                                   fmaxf(fabsf(g12.hi) + fabsf(g22.hi) + fabsf(g23.hi),
+                                         fabsf(g13.hi) + fabsf(g23.hi) + fabsf(g33.hi)));
+            const float mg = fmaxf(fabsf(gr.hi), fmaxf(fabsf(gs.hi), fabsf(gq.hi)));
+            const float C2 = bfp_offset(rs * mg * 1.00390625f);
+            float tr, lr, ts, ls, tt, lt;
+            bfp_first(tr, lr, C2, g11.hi, g11.lo, gr.hi, gr.lo);
+            bfp_first(ts, ls, C2, g12.hi, g12.lo, gr.hi, gr.lo);
+            bfp_first(tt, lt, C2, g13.hi, g13.lo, gr.hi, gr.lo);
+            bfp_term(tr, lr, g12.hi, g12.lo, gs.hi, gs.lo);
+            bfp_term(ts, ls, g22.hi, g22.lo, gs.hi, gs.lo);
+            bfp_term(tt, lt, g23.hi, g23.lo, gs.hi, gs.lo);
+            bfp_term(tr, lr, g13.hi, g13.lo, gq.hi, gq.lo);
+            bfp_term(ts, ls, g23.hi, g23.lo, gq.hi, gq.lo);
+            bfp_term(tt, lt, g33.hi, g33.lo, gq.hi, gq.lo);
+            sA[q] = {__fsub_rn(tr, C2), lr};
+            sB[q] = {__fsub_rn(ts, C2), ls};
+            gt[k] = {__fsub_rn(tt, C2), lt};
+            // h2 * (B * u): two Dekker products, errors gathered in lo
+            const float p2 = __fmul_rn(bm.hi, ru[k].hi);
+            float e2 = __fmaf_rn(bm.hi, ru[k].hi, -p2);
+            e2 = __fmaf_rn(bm.hi, ru[k].lo, e2);
+            e2 = __fmaf_rn(bm.lo, ru[k].hi, e2);
+            const float p3 = __fmul_rn(h2.hi, p2);
+            float e3 = __fmaf_rn(h2.hi, p2, -p3);
+            e3 = __fmaf_rn(h2.hi, e2, e3);
+            e3 = __fmaf_rn(h2.lo, p2, e3);
+            bu[k] = {p3, e3};
+        }
+    }
+    __syncthreads();
+
+    // ---- transpose: each line re-quantised to its largest value, then folded;
+    // r lines in place in sA, s lines in place in sB, t in registers
+    dfp wt[NP];
+    if (active) {
+        {
+            dfp x[NP], y[NP];
+            dfp *lr = sA + (j * NP + i) * LS;
+#pragma unroll
+            for (int l = 0; l < NP; ++l) x[l] = lr[l];
+            const float C3 = bfp_offset(__fmul_rn(T.kt, bfp_requantise<NP>(x)));
+            bfp_line<NP, 1>(x, y, [&](int) { return C3; }, T);
+#pragma unroll
+            for (int l = 0; l < NP; ++l) lr[l] = y[l];
+        }
+        {
+            dfp x[NP], y[NP];
+#pragma unroll
+            for (int l = 0; l < NP; ++l) x[l] = sB[(j * NP + l) * LS + i];
+            const float C3 = bfp_offset(__fmul_rn(T.kt, bfp_requantise<NP>(x)));
+            bfp_line<NP, 1>(x, y, [&](int) { return C3; }, T);
+#pragma unroll
+            for (int l = 0; l < NP; ++l) sB[(j * NP + l) * LS + i] = y[l];
+        }
+        const float C3 = bfp_offset(__fmul_rn(T.kt, bfp_requantise<NP>(gt)));
+        bfp_line<NP, 1>(gt, wt, [&](int) { return C3; }, T);
+    }
+    __syncthreads();
+
+    // ---- h1 (w_r + w_s + w_t) + h2 B u, rounded to FP64 and scaled by 2^E
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int p = k * NP2 + tid, q = (k * NP + j) * LS + i;
+            const dfp wr = sA[q], ws = sB[q];
+            // the three directions sit on different quanta: two-sums
+            float sl = __fadd_rn(__fadd_rn(wr.lo, ws.lo), wt[k].lo);
+            const float sh = bfp_two_sum(bfp_two_sum(wr.hi, ws.hi, sl), wt[k].hi, sl);
+            const float p1 = __fmul_rn(h1.hi, sh);
+            float e1 = __fmaf_rn(h1.hi, sh, -p1);
+            e1 = __fmaf_rn(h1.hi, sl, e1);
+            e1 = __fmaf_rn(h1.lo, sh, e1);
+            float lo = __fadd_rn(e1, bu[k].lo);
+            const float s = bfp_two_sum(p1, bu[k].hi, lo);
+            store(p, df_join_scaled({s, lo}, E));
+        }
+    }
+}
+
+// Host: the tables and the stage constants from the FP64 derivative matrix D
+// (row-major n x n, n even).
+static inline void ax_bfp_tables(int n, const double *D, BfpTabs *T)
+{
+    const int H = n / 2;
+    const double margin = 1.0 + 1.0 / 256;
+    double rsum_t = 0.0;
+    for (int dir = 0; dir < 2; ++dir)
+        for (int i = 0; i < H; ++i) {
+            double sa = 0.0, sb = 0.0;
+            for (int l = 0; l < H; ++l) {
+                // M = D (dir 0) or D^T (dir 1)
+                const double m0 = dir == 0 ? D[i * n + l] : D[l * n + i];
+                const double m1 = dir == 0 ? D[i * n + n - 1 - l] : D[(n - 1 - l) * n + i];
+                const double a = 0.5 * (m0 + m1), b = 0.5 * (m0 - m1);
+                const float ah = (float)a, bh = (float)b;
+                T->ah[dir][i][l] = ah;
+                T->al[dir][i][l] = (float)(a - (double)ah);
+                T->bh[dir][i][l] = bh;
+                T->bl[dir][i][l] = (float)(b - (double)bh);
+                sa += fabs(a);
+                sb += fabs(b);
+            }
+            if (dir == 0) {
+                // |e|, |o| <= 2 (inputs |X| <= 1): partial sums of row i <= 2 max(sa, sb) < 2^ex
+                int ex = 0;
+                frexp(2.0 * fmax(sa, sb) * margin, &ex);
+                T->cm_grad[i] = (float)ldexp(1.5, ex + 1);  // 1.5 * 2^23 * 2^(ex - 22)
+            } else {
+                rsum_t = fmax(rsum_t, fmax(sa, sb));
+            }
+        }
+    // transpose: |e|, |o| <= 2 M for a line whose largest input is M
+    T->kt = (float)(2.0 * rsum_t * margin);
+}

@@ -59,6 +59,7 @@ struct sem_ctx {
     void *geodf;       // float pairs of geo64 (FP64-accurate operator on FP32 pipes)
     void *tabdf;       // float pairs of D
     void *tabdfeo;     // float pairs of the folded half tables (even N+1)
+    void *bfp_tabs;    // host copy of the block-floating-point kernel's tables (even N+1)
     double *vert;      // device vertex grid [(nelz+1)(nely+1)(nelx+1)][3]
     double *jinv64;    // [E][9][n^3] dr_a/dx_c at a*3+c (allocated by the stepper)
     float *jinv32;

@@ -1,15 +1,16 @@
 // noalloc.cu -- a PCG entry point that allocates no memory at all.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph (a cudaMalloc there is illegal or breaks the
-// capture), code that runs under a memory manager that owns the whole device
-// budget (a framework's caching allocator, a plugin host, a real-time service
-// that pre-plans every byte), and code that must not pay cudaMalloc's implicit
-// device synchronisation.  sem_pcg_solve_noalloc serves them: it runs the same
-// persistent FP64 Jacobi-PCG kernel as sem_pcg_solve, without a context, with
-// every scratch vector, partial sum and solver state in the file-scope array
-// below.  The caller passes the inputs (geometry, right-hand side) and the
-// output (x); nothing is allocated by this file.
+// Some callers cannot call cudaMalloc: code that runs under a memory manager
+// that owns the whole device budget (a framework's caching allocator, a plugin
+// host, a real-time service that pre-plans every byte) and code that must not
+// pay cudaMalloc's implicit device synchronisation.  sem_pcg_solve_noalloc
+// serves them: it runs the persistent Jacobi-PCG kernel of sem_pcg_solve in
+// its native-FP64 mode (the arithmetic of sem_pcg_solve with inner =
+// SEM_F64_NATIVE), without a context, with every scratch vector, partial sum
+// and solver state in the file-scope array below.  The caller passes the
+// inputs (geometry, right-hand side) and the output (x); nothing is allocated
+// by this file.  The call reads the mesh volume back and synchronises the
+// caller's stream twice.
 #include <math.h>
 #include <string.h>
 
@@ -53,7 +54,10 @@ struct NaStateHost {
 };
 static_assert(sizeof(NaStateHost) <= NA_HEAD, "solver state exceeds its scratch slot");
 
-// Per-device host-side addresses of the scratch array (set up once per device).
+// Per-device device addresses of the scratch array, looked up once per device
+// (with that device current) by the first call there.  A cudaDeviceReset of the
+// device reloads the module and leaves the cached address stale, so calls after
+// a reset in the same process are not supported.
 static std::mutex g_noalloc_mu;
 static unsigned char *g_noalloc_addr[64];
 

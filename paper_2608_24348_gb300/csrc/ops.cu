@@ -17,7 +17,10 @@ int sem_launch_ax_df(const sem_ctx *c, const double *u, double *w, double h1, do
 // Per-order kernel choice (the tile shape of the stand-alone operator)
 // ---------------------------------------------------------------------------
 
-#define SEM_NVARIANT 3
+// Candidates per dtype: SEM_F32 three tile shapes; SEM_F64 three shapes of the
+// float-pair folded kernel and the block-floating-point kernel (3).
+#define SEM_NVARIANT 4
+static int sem_nvariant(sem_dtype dt) { return dt == SEM_F64 ? 4 : dt == SEM_F32 ? 3 : 1; }
 static int g_variant[SEM_NMAX + 1][5];  // 0 = not set -> built-in default
 static int g_variant_set[SEM_NMAX + 1][5];
 
@@ -40,8 +43,7 @@ int sem_ax_variant(int N, sem_dtype dt)
 extern "C" int sem_set_ax_variant(int N, sem_dtype dt, int variant)
 {
     if (N < 1 || N > SEM_NMAX || dt < SEM_F64 || dt > SEM_F64_NATIVE) return SEM_ERR_ARG;
-    if (variant < 0 || variant >= SEM_NVARIANT || (dt != SEM_F32 && dt != SEM_F64 && variant != 0))
-        return SEM_ERR_ARG;
+    if (variant < 0 || variant >= sem_nvariant(dt)) return SEM_ERR_ARG;
     g_variant[N][dt] = variant;
     g_variant_set[N][dt] = 1;
     return SEM_OK;
@@ -361,7 +363,7 @@ extern "C" int sem_tune_ax(sem_ctx *c, sem_dtype dt, int reps, double *ms, int *
     if (reps < 1) reps = 5;
     // FP32: three tile shapes; FP64-accurate, even N+1 <= 10: three elements-per-block
     // counts of the folded kernel; otherwise one candidate
-    const int nvar = dt == SEM_F32 || (dt == SEM_F64 && c->n % 2 == 0 && c->n <= 10) ? SEM_NVARIANT : 1;
+    const int nvar = dt == SEM_F32 || (dt == SEM_F64 && c->n % 2 == 0 && c->n <= 10) ? sem_nvariant(dt) : 1;
     if (ms)
         for (int v = 0; v < SEM_NVARIANT; ++v) ms[v] = -1.0;
     if (nvar == 1) {

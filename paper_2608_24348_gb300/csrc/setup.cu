@@ -303,6 +303,7 @@ extern "C" void sem_destroy(sem_ctx *c)
                   c->solve_dev, c->partials, c->stage[0], c->stage[1]};
     for (void *p : ps)
         if (p) cudaFree(p);
+    free(c->bfp_tabs);
     if (c->solve_host) cudaFreeHost(c->solve_host);
     for (int s = 0; s < 8; ++s) free_ws(c->ws[s]);
     free(c);

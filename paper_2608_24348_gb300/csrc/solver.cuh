@@ -23,7 +23,11 @@
 //   INIT32 unique  r32 = r / ||r||; d = 0; <r32,r32>, <r32,z32>
 //   A32    element d += alpha p32; p32 = z32 + beta p32; w32 = A32 p32; <p32,w32>
 //   C32    unique  r32 -= alpha dssum(w32); <r32,r32>, <r32,z32>
-//   UPD    local   x += ||r|| (d + alpha p32 when that last step is pending)
+//   UPD    local   p = x (kept until the next FP64 residual accepts the step);
+//                  x += ||r|| (d + alpha p32 when that last step is pending)
+//   XREST  local   x = p: a refinement step that raised the FP64 residual is
+//                  undone, so a solve never returns an iterate worse than the
+//                  one it had before that step
 //   FINAL  local   sum B x              (h2 == 0: remove the B-weighted mean)
 //   SHIFT  local   x -= sum(B x) / sum(B)
 // The inner product <a,b> = sum_local a b / mult is evaluated over unique
@@ -70,7 +74,7 @@ enum SolveMode { MODE_F64 = 0, MODE_F32 = 1, MODE_TC = 2, MODE_F64N = 3 };
 
 enum SolvePhase {
     PH_JAC = 0, PH_JACGS, PH_AX0, PH_R0, PH_A, PH_C, PH_R64, PH_INIT32, PH_A32, PH_C32, PH_UPD,
-    PH_FINAL, PH_SHIFT, PH_XUPD, PH_DONE
+    PH_FINAL, PH_SHIFT, PH_XUPD, PH_XREST, PH_DONE
 };
 
 struct ProbDesc {
@@ -147,7 +151,7 @@ __device__ __forceinline__ int phase_nvals(int ph)
 __device__ __forceinline__ int64_t phase_items(const ProbDesc &P, int ph)
 {
     switch (ph) {
-        case PH_JAC: case PH_UPD: case PH_FINAL: case PH_SHIFT: case PH_XUPD:
+        case PH_JAC: case PH_UPD: case PH_FINAL: case PH_SHIFT: case PH_XUPD: case PH_XREST:
             return (P.nL + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS;
         case PH_JACGS: case PH_R0: case PH_C: case PH_R64: case PH_INIT32: case PH_C32: {
             const int64_t nxch = (P.gs.ngx + SEM_SOLVE_THREADS - 1) / SEM_SOLVE_THREADS;
@@ -715,10 +719,17 @@ __device__ __forceinline__ void local_item(const ProbDesc &P, const PState &S, i
             P.minv[q] = P.h1 * s + P.h2 * g[6 * n3 + l];
         } break;
         case PH_UPD: {
+            // the FP64 p vector is unused by refinement: it keeps x until the
+            // next residual accepts the step
             float dv = __ldcg(P.d32 + q);
             if (S.pending) dv = fmaf((float)S.alpha, __ldcg(P.p32 + q), dv);
-            P.x[q] = fma(S.scale, (double)dv, __ldcg(P.x + q));
+            const double xo = __ldcg(P.x + q);
+            P.p[q] = xo;
+            P.x[q] = fma(S.scale, (double)dv, xo);
         } break;
+        case PH_XREST:
+            P.x[q] = __ldcg(P.p + q);
+            break;
         case PH_XUPD:
             P.x[q] = fma(S.alpha, __ldcg(P.p + q), __ldcg(P.x + q));
             break;
@@ -791,9 +802,17 @@ __device__ void advance(const SolveParams<MAXP> &prm, const ProbDesc &P, PState 
                 S.bnorm = sqrt(red[1]);
                 S.target = prm.abs_tol ? prm.tol : prm.tol * S.bnorm;
             }
+            if (rn <= S.target) { S.rnorm = rn; finish(SEM_OK); break; }
+            // a step that did not lower the FP64 residual (or made it non-finite)
+            // is undone: x returns to the iterate before it
+            if (S.outer > 0 && !(rn <= S.prev_rnorm)) {
+                S.rnorm = S.prev_rnorm;
+                S.status = SEM_ERR_NOT_CONVERGED;
+                S.phase = PH_XREST;
+                break;
+            }
             S.rnorm = rn;
             if (!isfinite(rn) || !isfinite(S.bnorm)) { finish(SEM_ERR_BREAKDOWN); break; }
-            if (rn <= S.target) { finish(SEM_OK); break; }
             if (S.outer >= prm.max_outer || S.iters >= prm.maxit) { finish(SEM_ERR_NOT_CONVERGED); break; }
             if (S.outer > 0 && rn > 0.5 * S.prev_rnorm) { finish(SEM_ERR_NOT_CONVERGED); break; }
             S.prev_rnorm = rn;
@@ -838,7 +857,7 @@ __device__ void advance(const SolveParams<MAXP> &prm, const ProbDesc &P, PState 
         case PH_UPD: S.outer += 1; S.phase = PH_AX0; break;
         case PH_FINAL: S.shift = red[0] / P.volume; S.phase = PH_SHIFT; break;
         case PH_SHIFT: S.phase = PH_DONE; break;
-        case PH_XUPD: S.phase = P.singular ? PH_FINAL : PH_DONE; break;
+        case PH_XUPD: case PH_XREST: S.phase = P.singular ? PH_FINAL : PH_DONE; break;
         default: S.phase = PH_DONE; break;
     }
     S.nvals = phase_nvals(S.phase);
@@ -927,7 +946,7 @@ __global__ void __launch_bounds__(SEM_SOLVE_THREADS, MODE == MODE_F32 ? SEM_SOLV
                 ElemDispatch<MODE, NPs...>::run(P, ph, S.alpha, S.beta, s_first[p], local,
                                                 prm.inner_tc, smem, acc);
             } else if (ph == PH_JAC || ph == PH_UPD || ph == PH_FINAL || ph == PH_SHIFT ||
-                       ph == PH_XUPD) {
+                       ph == PH_XUPD || ph == PH_XREST) {
                 local_item(P, S, ph, local, v);
             } else {
                 uniq_item(P, S, ph, local, v);

@@ -144,3 +144,21 @@ def test_pcg_full_size_pressure_poisson(sem):
         r, bn = m.residual(bo, x.cpu().numpy(), 1.0, 0.0)
         assert r <= 1.5e-10 * bn, (r, bn)
     assert rel(xm.cpu().numpy(), x64.cpu().numpy()) <= 1e-9
+
+
+def test_refinement_never_returns_a_worse_iterate(sem):
+    """BF16 tensor-core inner PCG on the 32^3, N=7 deformed pressure Poisson
+    problem: the 16-bit operator's error exceeds what the conditioning allows,
+    so a refinement step can raise the FP64 residual.  Such a step is undone:
+    the returned x is the best iterate (relative residual <= 1 from x0 = 0),
+    and the reported residual norm is that of the returned x (oracle check)."""
+    torch, dev = torch_dev()
+    ctx, m, _ = pair(sem, 7, (32, 32, 32), 0.1)
+    bg, bo = fourier_rhs(ctx, m)
+    x = torch.zeros_like(bg)
+    info = ctx.pcg_solve(bg, x, tol=1e-10, inner="bf16_tc", inner_tol=1e-2, max_outer=2)
+    assert info["status"] in (0, sem.ERR_NOT_CONVERGED), info
+    assert info["rnorm"] <= info["bnorm"] * (1 + 1e-12), info
+    r, bn = m.residual(bo, x.cpu().numpy(), 1.0, 0.0)
+    assert r <= bn * (1 + 1e-12)
+    assert abs(r - info["rnorm"]) <= 1e-6 * bn, (r, info)
