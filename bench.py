@@ -34,19 +34,14 @@ METRIC = "sem_ax GDOF/s & PCG solve ms at N=7, 32^3 elems: mixed vs FP64, 1 GB30
 BYTES_F64 = 72  # read u 8 + G 48 + B 8, write w 8
 BYTES_F32 = 36
 FLOPS_PER_NODE = 12 * (N_ORDER + 1) + 21  # FP64 flops of one operator application per node
-# FP32-pipe operations per node of the folded FP64-accurate operator at N=7:
-# six folded contractions of 48 ops per output (per half sum one exact product
-# of 4 and three compensated multiply-adds of 12; the un-normalised merge of 8
-# per output), three line folds of 8 per node before each contraction stage,
-# the geometric step (4 exact products, 6 multiply-adds), and the final sums,
-# weights and split of the FP64 join
-# (profiles/sem_ax_dfeo_24cubed_N7.md measures about 434 FMA-pipe ops per node)
-DF_OPS_PER_NODE = 6 * 48 + 2 * 3 * 8 + (4 * 4 + 6 * 12) + (2 * 8 + 4 + 12) + 2
-DF_KERNEL = "k_ax_dfeo<8,4,0>"
-# DRAM bytes per local node of k_ax_dfeo<8> (4 elements per block) from the ncu
-# capture on the 24^3 mesh (453.33 MB read + 48.27 MB written for 7,077,888
-# nodes), scaled to the 32^3 mesh
-DF_TRAFFIC_PER_NODE = (453.33e6 + 48.27e6) / 7077888
+# The FP64-accurate operator at N=7 is the block-floating-point kernel with u
+# staged by bulk copies, one element per block (the library default):
+# instructions per node from the ncu capture on the 24^3 mesh (all pipes),
+# DRAM bytes per node from the same capture (453.33 MB read + 47.84 MB written
+# for 7,077,888 nodes), scaled to the 32^3 mesh
+DF_KERNEL = "k_ax_bfp_st<8,0,1,16>"
+DF_INSTR_PER_NODE = 421
+DF_TRAFFIC_PER_NODE = (453.33e6 + 47.84e6) / 7077888
 FP64_PROBE_TFLOPS = 1.26  # FP64 FMA rate measured on this GPU model (probe: 2.2 FMA/clk/SM)
 
 
@@ -343,7 +338,7 @@ def main():
     mhz = clk.get("sm_max_mhz") or pk["sm_max_mhz"]
     fp32_peak = 128 * n_sms * mhz * 1e6 / 1e12          # FP32-pipe ops/s (T)
     fp64_peak = FP64_PROBE_TFLOPS
-    df_ops = DF_OPS_PER_NODE * nL / (avg64 * 1e-3) / 1e12
+    df_ops = DF_INSTR_PER_NODE * nL / (avg64 * 1e-3) / 1e12
     avg_nat = statistics.mean(per_nat)
     avg32 = statistics.mean(per32)
     hbm = lambda B, ms: B * nL / (ms * 1e-3) / 1e9
@@ -374,9 +369,10 @@ def main():
                      "unit": "GB/s", "frac": hbm(BYTES_F64, avg64) / pk["hbm_gbs"],
                      "traffic": DF_TRAFFIC_PER_NODE * nL, "peak_src": pk["src"],
                      "kernel": DF_KERNEL, "bytes_per_node": BYTES_F64,
-                     "alu": {"achieved": df_ops, "peak": fp32_peak, "unit": "Tops/s",
-                             "frac": df_ops / fp32_peak, "ops_per_node": DF_OPS_PER_NODE,
-                             "peak_src": "128 FP32-pipe ops/clk/SM x SMs x max SM clock"}},
+                     "issue": {"achieved": df_ops, "peak": fp32_peak, "unit": "T thread-instr/s",
+                               "frac": df_ops / fp32_peak, "instr_per_node": DF_INSTR_PER_NODE,
+                               "peak_src": "one warp instruction per clock per SM sub-partition "
+                                           "(128 thread-instr/clk/SM) x SMs x max SM clock"}},
         "native_f64": {"gdofs": gdof(barrier_max(tot_nat, ws) / k2),
                        "roofline": {"bound": "alu", "unit": "TFLOP/s",
                                     "achieved": FLOPS_PER_NODE * nL / (avg_nat * 1e-3) / 1e12,

@@ -70,10 +70,12 @@ typedef enum {
     SEM_F64_NATIVE = 4 /* FP64 storage, native FP64 FMA arithmetic */
 } sem_dtype;
 /* SEM_F64 in sem_ax evaluates the FP64 operator on the FP32 pipes with
- * error-free transformations (float pairs, compensated sums, per-element
- * power-of-two scaling); it meets the same FP64 accuracy bar as
- * SEM_F64_NATIVE and is several times faster on parts whose FP64 rate is a
- * small fraction of their FP32 rate. */
+ * error-free transformations (per-element block-floating-point pairs with
+ * exact folds and fused exact-product accumulation for odd N <= 11, float
+ * pairs with compensated sums otherwise; per-element power-of-two scaling);
+ * it meets the same FP64 accuracy bar as SEM_F64_NATIVE (max error <= 1e-12
+ * of the largest output) and is several times faster on parts whose FP64
+ * rate is a small fraction of their FP32 rate. */
 
 typedef struct sem_ctx sem_ctx;
 typedef struct sem_tgv sem_tgv;
@@ -137,22 +139,33 @@ SEM_API int sem_geom(sem_ctx *ctx, double *out, void *stream);
 SEM_API int sem_ax(sem_ctx *ctx, const void *u, void *w, double h1, double h2, sem_dtype dtype,
            void *stream);
 
+/* Entries of sem_tune_ax's ms array. */
+#define SEM_TUNE_MAX 16
+
 /* Autotuner of sem_ax's kernel choice for the context's order N and dtype.
- * Times every candidate tile shape (for SEM_F32: 0 = direct loads, 1 =
- * bulk-copy staged, 256 threads x 2 stages, 2 = staged, 128 threads x 3
- * stages; for SEM_F64 with even N+1 <= 10, the folded float-pair kernel with
- * 0 = 256/(N+1)^2 elements per block and block-wide barriers, 1 = the same
- * with one hardware barrier per element where (N+1)^2 is a multiple of 32
- * (else as 0), 2 = half the elements per block (at least one); other cases
- * have one candidate, reported as 0 ms) reps times on
- * the context's solver workspace (scratch between solves; no allocation),
- * stores the fastest for this process and returns it in *best; ms (may be
- * NULL, else 3 entries) receives the average time of each candidate (-1 where
- * a candidate does not apply).  Synchronous. */
+ * Times every candidate kernel and tile shape reps times on the context's
+ * solver workspace (scratch between solves; no allocation), stores the
+ * fastest for this process and returns it in *best; ms (NULL, or
+ * SEM_TUNE_MAX entries) receives the average time of each candidate (-1
+ * where a candidate does not apply).  Synchronous.  Candidates:
+ *  - SEM_F32: 0 = direct loads, 1 = bulk-copy staged, 256 threads x 2 stages,
+ *    2 = staged, 128 threads x 3 stages;
+ *  - SEM_F64 with even N+1 <= 12: the float-pair folded kernel with
+ *    0 = 256/(N+1)^2 elements per block and block-wide barriers, 1 = one
+ *    hardware barrier per element where (N+1)^2 is a multiple of 32 (else as
+ *    0), 2 = half the elements per block; the block-floating-point kernel
+ *    with 3 = direct loads, 4 = direct loads and paired f32x2 instructions,
+ *    5 = u staged by bulk copies, 6 = staged and paired, 7 = staged with half
+ *    the elements per block, 8 = staged with one element per block,
+ *    9 and 10 = as 8 with register budgets for 20 and 24 warps per SM
+ *    (the staged forms fall back to 3 or 4 for u in host memory or not
+ *    16-byte aligned);
+ *  - other cases have one candidate, reported as 0 ms. */
 SEM_API int sem_tune_ax(sem_ctx *ctx, sem_dtype dtype, int reps, double *ms, int *best);
 
 /* Selects sem_ax's kernel for order N and dtype in this process (e.g. from a
- * cached tuning result).  Until set, a built-in per-order default applies. */
+ * cached tuning result); -1 restores the built-in per-order default, which
+ * applies until a variant is set. */
 SEM_API int sem_set_ax_variant(int N, sem_dtype dtype, int variant);
 
 /* Direct-stiffness sum in place (Sec. 2, gather/scatter): every local copy of

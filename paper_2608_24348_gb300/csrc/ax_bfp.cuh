@@ -52,12 +52,13 @@ struct BfpCfg {
 };
 
 // Folded half tables of D (index 0, gradient) and D^T (index 1), hi and lo
-// parts: A_il = (M_il + M_{i,N-l})/2, B_il = (M_il - M_{i,N-l})/2 for l < H.
-// Passed by value as a kernel parameter: the unrolled loops index it with
-// constants, so every table entry is a constant-bank operand.
+// parts: A_il = (M_il + M_{i,N-l})/2, B_il = (M_il - M_{i,N-l})/2 for l < H,
+// stored as (A, B) pairs.  Passed by value as a kernel parameter: the
+// unrolled loops index it with constants, so every entry is a constant-bank
+// operand.
 struct BfpTabs {
-    float ah[2][SEM_NPMAX / 2][SEM_NPMAX / 2], al[2][SEM_NPMAX / 2][SEM_NPMAX / 2];
-    float bh[2][SEM_NPMAX / 2][SEM_NPMAX / 2], bl[2][SEM_NPMAX / 2][SEM_NPMAX / 2];
+    float2 h[2][SEM_NPMAX / 2][SEM_NPMAX / 2];  // (A_il, B_il) hi parts
+    float2 l[2][SEM_NPMAX / 2][SEM_NPMAX / 2];  // (A_il, B_il) lo parts
     float cm_grad[SEM_NPMAX / 2];  // gradient stage: accumulator offset of output row i (|X| <= 1)
     float kt;       // transpose stage: bound of its partial sums per unit of the line's largest input
 };
@@ -120,12 +121,12 @@ __device__ __forceinline__ void bfp_line(const dfp (&x)[NP], dfp (&y)[NP], const
     for (int i = 0; i < H; ++i) {
         const float C = off(i), C2 = __fadd_rn(C, C);
         float ta, la, tb, lb;
-        bfp_first(ta, la, C, T.ah[DIR][i][0], T.al[DIR][i][0], eh[0], el[0]);
-        bfp_first(tb, lb, C, T.bh[DIR][i][0], T.bl[DIR][i][0], oh[0], ol[0]);
+        bfp_first(ta, la, C, T.h[DIR][i][0].x, T.l[DIR][i][0].x, eh[0], el[0]);
+        bfp_first(tb, lb, C, T.h[DIR][i][0].y, T.l[DIR][i][0].y, oh[0], ol[0]);
 #pragma unroll
         for (int l = 1; l < H; ++l) {
-            bfp_term(ta, la, T.ah[DIR][i][l], T.al[DIR][i][l], eh[l], el[l]);
-            bfp_term(tb, lb, T.bh[DIR][i][l], T.bl[DIR][i][l], oh[l], ol[l]);
+            bfp_term(ta, la, T.h[DIR][i][l].x, T.l[DIR][i][l].x, eh[l], el[l]);
+            bfp_term(tb, lb, T.h[DIR][i][l].y, T.l[DIR][i][l].y, oh[l], ol[l]);
         }
         // ta = C + a, tb = C + b:  y_i = a + b,  y_{N-i} = b - a (all exact on the grid)
         y[i].hi = __fadd_rn(ta, __fsub_rn(tb, C2));
@@ -133,6 +134,92 @@ __device__ __forceinline__ void bfp_line(const dfp (&x)[NP], dfp (&y)[NP], const
         y[NP - 1 - i].hi = __fsub_rn(tb, ta);
         y[NP - 1 - i].lo = __fsub_rn(lb, la);
     }
+}
+
+// Packed pairs of floats for the sm_100-family paired FP32 instructions
+// (fma/add/sub.rn.f32x2: two IEEE round-to-nearest operations per lane in
+// one instruction; the FMA pipes' rate is unchanged, the issue slots halve).
+typedef unsigned long long bfp_f2;
+
+__device__ __forceinline__ bfp_f2 bfp_pk(float a, float b)
+{
+    bfp_f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void bfp_upk(bfp_f2 r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ bfp_f2 bfp_fma2(bfp_f2 a, bfp_f2 b, bfp_f2 c)
+{
+    bfp_f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ bfp_f2 bfp_add2(bfp_f2 a, bfp_f2 b)
+{
+    bfp_f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ bfp_f2 bfp_sub2(bfp_f2 a, bfp_f2 b)
+{
+    bfp_f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ bfp_f2 bfp_f2of(float2 v) { return bfp_pk(v.x, v.y); }
+
+// bfp_line with the even (A) and odd (B) chains of each output row packed
+// into one instruction stream: the same operations and roundings lane by lane.
+template <int NP, int DIR, class Off>
+__device__ __forceinline__ void bfp_line2(const dfp (&x)[NP], dfp (&y)[NP], const Off &off,
+                                          const BfpTabs &T)
+{
+    constexpr int H = NP / 2;
+    bfp_f2 eo[H], eol[H];  // (e_l, o_l) grid parts and remainders
+#pragma unroll
+    for (int l = 0; l < H; ++l) {
+        eo[l] = bfp_pk(__fadd_rn(x[l].hi, x[NP - 1 - l].hi), __fsub_rn(x[l].hi, x[NP - 1 - l].hi));
+        eol[l] = bfp_pk(__fadd_rn(x[l].lo, x[NP - 1 - l].lo), __fsub_rn(x[l].lo, x[NP - 1 - l].lo));
+    }
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const float C = off(i), C2 = __fadd_rn(C, C);
+        const bfp_f2 CC = bfp_pk(C, C);
+        bfp_f2 th = bfp_f2of(T.h[DIR][i][0]);
+        bfp_f2 t = bfp_fma2(th, eo[0], CC);
+        bfp_f2 lo = bfp_fma2(th, eo[0], bfp_sub2(CC, t));
+        lo = bfp_fma2(th, eol[0], lo);
+        lo = bfp_fma2(bfp_f2of(T.l[DIR][i][0]), eo[0], lo);
+#pragma unroll
+        for (int l = 1; l < H; ++l) {
+            th = bfp_f2of(T.h[DIR][i][l]);
+            const bfp_f2 tn = bfp_fma2(th, eo[l], t);
+            lo = bfp_add2(lo, bfp_fma2(th, eo[l], bfp_sub2(t, tn)));
+            lo = bfp_fma2(th, eol[l], lo);
+            lo = bfp_fma2(bfp_f2of(T.l[DIR][i][l]), eo[l], lo);
+            t = tn;
+        }
+        float ta, tb, la, lb;
+        bfp_upk(t, ta, tb);
+        bfp_upk(lo, la, lb);
+        y[i].hi = __fadd_rn(ta, __fsub_rn(tb, C2));
+        y[i].lo = __fadd_rn(la, lb);
+        y[NP - 1 - i].hi = __fsub_rn(tb, ta);
+        y[NP - 1 - i].lo = __fsub_rn(lb, la);
+    }
+}
+
+template <int NP, int DIR, bool PAIR, class Off>
+__device__ __forceinline__ void bfp_line_sel(const dfp (&x)[NP], dfp (&y)[NP], const Off &off,
+                                             const BfpTabs &T)
+{
+    if constexpr (PAIR)
+        bfp_line2<NP, DIR>(x, y, off, T);
+    else
+        bfp_line<NP, DIR>(x, y, off, T);
 }
 
 // Largest value of m over one element's threads; slot: NE x 8 words.  The
@@ -199,13 +286,15 @@ __device__ __forceinline__ float bfp_two_sum(float a, float b, float &err)
 
 // One element.  load(p) -> double (u at local node p), store(p, double).
 // geo: the element's float-pair factors [7][NP^3].  slab: 3 slabs; red: 8
-// words (the exponent reduction).  All threads of the block call it (barriers
-// are block-wide).
-template <int NP, class Load, class Store>
+// words (the exponent reduction).  after_load() runs on every thread after
+// the first block barrier, when no thread reads u any more.  All threads of
+// the block call it (barriers are block-wide).
+template <int NP, bool PAIR, class Load, class Store, class After>
 __device__ __forceinline__ void ax_bfp_element(const Load &load, const Store &store,
                                                const dfp *__restrict__ geo, dfp h1, dfp h2,
                                                const BfpTabs &T, dfp *__restrict__ slab,
-                                               unsigned *red, int tid, bool active)
+                                               unsigned *red, int tid, bool active,
+                                               const After &after_load)
 {
     using Cf = BfpCfg<NP>;
     constexpr int NP2 = Cf::NP2, NP3 = Cf::NP3, LS = Cf::LS, SL = Cf::SLAB;
@@ -224,6 +313,7 @@ __device__ __forceinline__ void ax_bfp_element(const Load &load, const Store &st
     }
     bfp_group_max_write<NP>(m, red, tid);
     __syncthreads();
+    after_load();
     const unsigned bmax = bfp_group_max_read<NP>(red);
     // u 2^-E has |.| < 1
     const int E = bmax > 0 ? (int)bmax - 1022 : 0;
@@ -251,7 +341,7 @@ __device__ __forceinline__ void ax_bfp_element(const Load &load, const Store &st
             const dfp *lr = su + (j * NP + i) * LS;
 #pragma unroll
             for (int l = 0; l < NP; ++l) x[l] = lr[l];
-            bfp_line<NP, 0>(x, y, off, T);
+            bfp_line_sel<NP, 0, PAIR>(x, y, off, T);
             dfp *or_ = sA + (j * NP + i) * LS;
 #pragma unroll
             for (int l = 0; l < NP; ++l) or_[l] = y[l];
@@ -260,11 +350,11 @@ __device__ __forceinline__ void ax_bfp_element(const Load &load, const Store &st
             dfp x[NP], y[NP];
 #pragma unroll
             for (int l = 0; l < NP; ++l) x[l] = su[(j * NP + l) * LS + i];
-            bfp_line<NP, 0>(x, y, off, T);
+            bfp_line_sel<NP, 0, PAIR>(x, y, off, T);
 #pragma unroll
             for (int l = 0; l < NP; ++l) sB[(j * NP + l) * LS + i] = y[l];
         }
-        bfp_line<NP, 0>(ru, gt, off, T);
+        bfp_line_sel<NP, 0, PAIR>(ru, gt, off, T);
     }
     __syncthreads();
 
@@ -322,7 +412,7 @@ __device__ __forceinline__ void ax_bfp_element(const Load &load, const Store &st
 #pragma unroll
             for (int l = 0; l < NP; ++l) x[l] = lr[l];
             const float C3 = bfp_offset(__fmul_rn(T.kt, bfp_requantise<NP>(x)));
-            bfp_line<NP, 1>(x, y, [&](int) { return C3; }, T);
+            bfp_line_sel<NP, 1, PAIR>(x, y, [&](int) { return C3; }, T);
 #pragma unroll
             for (int l = 0; l < NP; ++l) lr[l] = y[l];
         }
@@ -331,12 +421,12 @@ __device__ __forceinline__ void ax_bfp_element(const Load &load, const Store &st
 #pragma unroll
             for (int l = 0; l < NP; ++l) x[l] = sB[(j * NP + l) * LS + i];
             const float C3 = bfp_offset(__fmul_rn(T.kt, bfp_requantise<NP>(x)));
-            bfp_line<NP, 1>(x, y, [&](int) { return C3; }, T);
+            bfp_line_sel<NP, 1, PAIR>(x, y, [&](int) { return C3; }, T);
 #pragma unroll
             for (int l = 0; l < NP; ++l) sB[(j * NP + l) * LS + i] = y[l];
         }
         const float C3 = bfp_offset(__fmul_rn(T.kt, bfp_requantise<NP>(gt)));
-        bfp_line<NP, 1>(gt, wt, [&](int) { return C3; }, T);
+        bfp_line_sel<NP, 1, PAIR>(gt, wt, [&](int) { return C3; }, T);
     }
     __syncthreads();
 
@@ -376,10 +466,8 @@ static inline void ax_bfp_tables(int n, const double *D, BfpTabs *T)
                 const double m1 = dir == 0 ? D[i * n + n - 1 - l] : D[(n - 1 - l) * n + i];
                 const double a = 0.5 * (m0 + m1), b = 0.5 * (m0 - m1);
                 const float ah = (float)a, bh = (float)b;
-                T->ah[dir][i][l] = ah;
-                T->al[dir][i][l] = (float)(a - (double)ah);
-                T->bh[dir][i][l] = bh;
-                T->bl[dir][i][l] = (float)(b - (double)bh);
+                T->h[dir][i][l] = make_float2(ah, bh);
+                T->l[dir][i][l] = make_float2((float)(a - (double)ah), (float)(b - (double)bh));
                 sa += fabs(a);
                 sb += fabs(b);
             }

@@ -132,65 +132,16 @@ constexpr int dfeo_group_sync()
     return (NP * NP) % 32 == 0 && NE0 >= 2 && NE0 <= 15 && NP <= 10 ? NP * NP : 0;
 }
 
-// Block-floating-point variant (ax_bfp.cuh) for even NP: NE elements per block
-// of at most 256 threads, two blocks per SM (128 registers a thread).
-template <int NP>
-__global__ void __launch_bounds__(BfpCfg<NP>::THREADS, 2)
-    k_ax_bfp(const double *__restrict__ u, double *__restrict__ w, const dfp *__restrict__ geo,
-             const __grid_constant__ BfpTabs T, dfp h1, dfp h2, int64_t E, const double *upf)
-{
-    using C = BfpCfg<NP>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    dfp *slabs = reinterpret_cast<dfp *>(smem_raw);
-    unsigned *red = reinterpret_cast<unsigned *>(slabs + (size_t)C::NE * 3 * C::SLAB);
-    const int grp = threadIdx.x / C::NP2, tid = threadIdx.x - grp * C::NP2;
-    for (int t = threadIdx.x; t < 8 * C::NE; t += blockDim.x) red[t] = 0u;
-    __syncthreads();
-    for (int64_t e0 = (int64_t)blockIdx.x * C::NE; e0 < E; e0 += (int64_t)gridDim.x * C::NE) {
-        df_prefetch<NP>(upf, geo, e0, e0 + (int64_t)gridDim.x * C::NE, C::NE, E);
-        const int64_t e = e0 + grp;
-        const bool active = e < E;
-        const int64_t off = (active ? e : 0) * C::NP3;
-        const double *ue = u + off;
-        double *we = w + off;
-        auto load = [&](int p) { return ue[p]; };
-        auto store = [&](int p, double v) { we[p] = v; };
-        ax_bfp_element<NP>(load, store, geo + (active ? e : 0) * 7 * C::NP3, h1, h2, T,
-                           slabs + (size_t)grp * 3 * C::SLAB, red + grp * 8, tid, active);
-    }
-}
-
-template <int NP>
-static int launch_bfp(const sem_ctx *c, const double *u, double *w, dfp H1, dfp H2, cudaStream_t s)
-{
-    using C = BfpCfg<NP>;
-    if (!c->bfp_tabs) return SEM_ERR_ARG;
-    const size_t smem = ax_bfp_smem_bytes_ne<NP, C::NE>();
-    static std::atomic<unsigned> attr{0};
-    SEM_CUDA(sem_smem_attr(k_ax_bfp<NP>, smem, attr));
-    int per_sm = 0;
-    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_bfp<NP>, C::THREADS, smem));
-    if (per_sm < 1) return SEM_ERR_ARG;
-    int64_t groups = sem_ceil_div(c->E, C::NE);
-    int64_t grid = (int64_t)per_sm * c->num_sms;
-    if (grid > groups) grid = groups;
-    k_ax_bfp<NP><<<(unsigned)grid, C::THREADS, smem, s>>>(u, w, (const dfp *)c->geodf,
-                                                          *(const BfpTabs *)c->bfp_tabs, H1, H2, c->E,
-                                                          c->u_sysmem ? nullptr : u);
-    SEM_CHECK_LAUNCH();
-    return SEM_OK;
-}
+int sem_launch_ax_bfp(const sem_ctx *c, int variant, const double *u, double *w, double h1,
+                      double h2, cudaStream_t s);  // ax_bfp.cu
 
 template <int NP>
 static int launch_df(const sem_ctx *c, const double *u, double *w, double h1, double h2,
                      cudaStream_t s)
 {
-    if constexpr (BfpCfg<NP>::OK) {
-        if (sem_ax_variant(c->N, SEM_F64) == 3 && ax_bfp_smem_bytes_ne<NP, BfpCfg<NP>::NE>() <= 227 * 1024) {
-            const float a = (float)h1, b = (float)h2;
-            const dfp H1 = {a, (float)(h1 - (double)a)}, H2 = {b, (float)(h2 - (double)b)};
-            return launch_bfp<NP>(c, u, w, H1, H2, s);
-        }
+    if (sem_ax_variant(c->N, SEM_F64) >= 3) {
+        const int rc = sem_launch_ax_bfp(c, sem_ax_variant(c->N, SEM_F64), u, w, h1, h2, s);
+        if (rc != SEM_ERR_ARG) return rc;  // else the order has no block-floating-point kernel
     }
     if constexpr (AxEoCfg<NP>::OK) {
         if (ax_dfeo_smem_bytes<NP>() <= 227 * 1024) {

@@ -18,16 +18,24 @@ int sem_launch_ax_df(const sem_ctx *c, const double *u, double *w, double h1, do
 // ---------------------------------------------------------------------------
 
 // Candidates per dtype: SEM_F32 three tile shapes; SEM_F64 three shapes of the
-// float-pair folded kernel and the block-floating-point kernel (3).
-#define SEM_NVARIANT 4
-static int sem_nvariant(sem_dtype dt) { return dt == SEM_F64 ? 4 : dt == SEM_F32 ? 3 : 1; }
+// float-pair folded kernel and the block-floating-point kernel with scalar (3)
+// and paired (4) FP32 instructions, each also with u staged by bulk copies (5, 6),
+// and the staged scalar form with half (7) and one (8) element per block, the
+// latter also with register budgets for 20 (9) and 24 (10) warps per SM.
+#define SEM_NVARIANT 11
+static_assert(SEM_NVARIANT <= SEM_TUNE_MAX, "tuner output array");
+static int sem_nvariant(sem_dtype dt) { return dt == SEM_F64 ? 11 : dt == SEM_F32 ? 3 : 1; }
 static int g_variant[SEM_NMAX + 1][5];  // 0 = not set -> built-in default
 static int g_variant_set[SEM_NMAX + 1][5];
 
-// Built-in defaults from measurements on GB300: staged 128 x 3 for N = 7 and
-// 9, staged 256 x 2 for N = 3 and 5, direct loads otherwise.
+// Built-in defaults from measurements on GB300.  FP32: staged 128 x 3 for
+// N = 7 and 9, staged 256 x 2 for N = 3 and 5, direct loads otherwise.
+// FP64-accurate: the block-floating-point kernel with u staged, one element
+// per block (0.27 ms against 0.43 ms for the float-pair folded kernel at 32^3,
+// N = 7), for odd N <= 11 (even N+1 <= 12); the float-pair kernels otherwise.
 static int default_variant(int N, sem_dtype dt)
 {
+    if (dt == SEM_F64) return (N % 2 == 1 && N <= 11) ? 8 : 0;
     if (dt != SEM_F32) return 0;
     if (N == 7 || N == 9) return 2;
     if (N == 3 || N == 5) return 1;
@@ -43,6 +51,10 @@ int sem_ax_variant(int N, sem_dtype dt)
 extern "C" int sem_set_ax_variant(int N, sem_dtype dt, int variant)
 {
     if (N < 1 || N > SEM_NMAX || dt < SEM_F64 || dt > SEM_F64_NATIVE) return SEM_ERR_ARG;
+    if (variant == -1) {  // back to the built-in default
+        g_variant_set[N][dt] = 0;
+        return SEM_OK;
+    }
     if (variant < 0 || variant >= sem_nvariant(dt)) return SEM_ERR_ARG;
     g_variant[N][dt] = variant;
     g_variant_set[N][dt] = 1;
@@ -363,7 +375,7 @@ extern "C" int sem_tune_ax(sem_ctx *c, sem_dtype dt, int reps, double *ms, int *
     if (reps < 1) reps = 5;
     // FP32: three tile shapes; FP64-accurate, even N+1 <= 10: three elements-per-block
     // counts of the folded kernel; otherwise one candidate
-    const int nvar = dt == SEM_F32 || (dt == SEM_F64 && c->n % 2 == 0 && c->n <= 10) ? sem_nvariant(dt) : 1;
+    const int nvar = dt == SEM_F32 || (dt == SEM_F64 && c->n % 2 == 0 && c->n <= 12) ? sem_nvariant(dt) : 1;
     if (ms)
         for (int v = 0; v < SEM_NVARIANT; ++v) ms[v] = -1.0;
     if (nvar == 1) {

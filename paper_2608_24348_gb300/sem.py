@@ -21,6 +21,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_BAD_MESH, ERR_NOT_CONVERGED, ERR_BREAKDOWN
     0, -1, -2, -3, -4, -5, -6, -7
 ERR_TOO_LARGE = -8
 NOALLOC_MAX_NODES = 1000000
+TUNE_MAX = 16  # entries of sem_tune_ax's ms array (SEM_TUNE_MAX)
 
 _lib = None
 _lock = threading.Lock()
@@ -299,7 +300,8 @@ def pcg_solve_noalloc(N, nel, periodic, geom, b, x, h1=1.0, h2=0.0, stream=None,
 
 
 def set_ax_variant(N, dtype, variant):
-    """Select sem_ax's kernel for order N and dtype in this process."""
+    """Select sem_ax's kernel for order N and dtype in this process (-1: the
+    built-in default)."""
     L = load()
     _check(L.sem_set_ax_variant(int(N), DTYPES[dtype] if isinstance(dtype, str) else int(dtype),
                                 int(variant)), "sem_set_ax_variant")
@@ -323,10 +325,10 @@ def autotune(ctx, dtype="f32", reps=5, cache=None):
         if key in table:
             set_ax_variant(ctx.N, dt, table[key]["variant"])
             return dict(table[key], cached=True)
-    ms = (ctypes.c_double * 8)(*([-1.0] * 8))
+    ms = (ctypes.c_double * TUNE_MAX)(*([-1.0] * TUNE_MAX))
     best = ctypes.c_int()
     _check(L.sem_tune_ax(ctx.handle, dt, int(reps), ms, ctypes.byref(best)), "sem_tune_ax")
-    out = {"variant": best.value, "ms": [ms[i] for i in range(3) if ms[i] >= 0]}
+    out = {"variant": best.value, "ms": [ms[i] for i in range(TUNE_MAX) if ms[i] >= 0]}
     if cache:
         table[key] = out
         os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)

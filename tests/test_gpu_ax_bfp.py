@@ -1,5 +1,8 @@
-"""The block-floating-point FP64-accurate operator (sem_ax SEM_F64, kernel
-candidate 3, even N+1) against the FP64 oracle.
+"""The block-floating-point FP64-accurate operator (sem_ax SEM_F64 for even
+N+1 <= 12: its candidates 3 and 4 (direct loads; scalar or paired f32x2
+instructions), 5 and 6 (u staged by bulk copies), 8 (staged, one element per
+block, the default) and 9, 10 (other register budgets)) against the FP64
+oracle.
 
 Bar: max|gpu - ref| / max|ref| <= 1e-12, the FP64 operator's bar.  Cases span
 every even N+1 the kernel serves, several element groups and a ragged tail,
@@ -18,7 +21,7 @@ from paper_2608_24348_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TWO_PI = 2 * math.pi
-BFP = 3
+BFP = (3, 4, 5, 6, 8, 9, 10)
 
 
 def torch_dev():
@@ -37,16 +40,22 @@ def make(sem, N, nel, perturb, periodic=(1, 1, 1)):
 
 
 def run(sem, ctx, u, h1, h2):
+    """Every candidate's result; the two are bit-identical (same roundings)."""
     torch, dev = torch_dev()
     ud = torch.from_numpy(np.ascontiguousarray(u)).to(dev)
-    wd = torch.empty_like(ud)
-    sem.set_ax_variant(ctx.N, "f64", BFP)
-    try:
-        ctx.ax(ud, wd, h1, h2, "f64")
-        torch.cuda.synchronize()
-    finally:
-        sem.set_ax_variant(ctx.N, "f64", 0)
-    return wd.cpu().numpy()
+    outs = []
+    for v in BFP:
+        wd = torch.empty_like(ud)
+        sem.set_ax_variant(ctx.N, "f64", v)
+        try:
+            ctx.ax(ud, wd, h1, h2, "f64")
+            torch.cuda.synchronize()
+        finally:
+            sem.set_ax_variant(ctx.N, "f64", -1)
+        outs.append(wd.cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    return outs[0]
 
 
 @pytest.mark.parametrize("N,nel,perturb", [(1, (3, 2, 5), 0.1), (3, (2, 3, 2), 0.15),

@@ -125,9 +125,12 @@ def test_autotuner_candidates_keep_parity(sem, tmp_path):
 
 
 def test_autotuner_f64_candidates_keep_parity(sem):
-    """The elements-per-block candidates of the FP64-accurate folded kernel (even
-    N+1) give results within the FP64 bar of the oracle, identical to each
-    other; odd N+1 has one candidate."""
+    """Every candidate of the FP64-accurate operator (even N+1: three shapes of the
+    float-pair folded kernel, eight of the block-floating-point kernel) is within
+    the FP64 bar of the oracle; candidates of one kernel family are identical to
+    each other (the grouping of elements into blocks, the staging of u and the
+    pairing of instructions do not enter the arithmetic); odd N+1 has one
+    candidate."""
     torch, dev = torch_dev()
     for N, nel in ((7, (5, 4, 3)), (5, (4, 4, 5)), (1, (3, 3, 3))):
         ctx, m, _ = make(sem, N, nel, 0.1)
@@ -135,21 +138,24 @@ def test_autotuner_f64_candidates_keep_parity(sem):
         ref = m.ax(u, 0.3, 2.0)
         ud = torch.from_numpy(u).to(dev)
         outs = []
-        for v in range(3):
+        for v in range(11):
             sem.set_ax_variant(N, "f64", v)
             wd = torch.empty_like(ud)
             ctx.ax(ud, wd, 0.3, 2.0, "f64")
             outs.append(wd.cpu().numpy())
             assert rel_err(outs[-1], ref) <= 1e-12, (N, v)
-        # the grouping of elements into blocks does not enter the arithmetic
-        assert np.array_equal(outs[1], outs[0]) and np.array_equal(outs[2], outs[0]), N
+        for v in (1, 2):
+            assert np.array_equal(outs[v], outs[0]), (N, v)
+        for v in range(4, 11):
+            assert np.array_equal(outs[v], outs[3]), (N, v)
         r = sem.autotune(ctx, "f64")
-        assert r["variant"] in (0, 1, 2) and len(r["ms"]) == 3 and min(r["ms"]) > 0, r
-        sem.set_ax_variant(N, "f64", 0)
+        assert 0 <= r["variant"] <= 10 and len(r["ms"]) == 11 and min(r["ms"]) > 0, r
+        sem.set_ax_variant(N, "f64", -1)
         assert ctx.device_status() == 0
     ctx, _, _ = make(sem, 4, (3, 3, 3), 0.1)
     r = sem.autotune(ctx, "f64")
     assert r["variant"] == 0 and r["ms"] == [0.0], r
+    sem.set_ax_variant(4, "f64", -1)
 
 
 def test_ax_host_pointers(sem):
