@@ -5,60 +5,13 @@
 Kernels: ax_f64, ax_f32, ax_bf16_tc, dssum, pcg_f64, pcg_f32 (a bounded number
 of PCG iterations), tgv_f64, tgv_f32 (steps of the Taylor-Green stepper).
 The mesh is the benchmark's: nel^3 elements, order N, interior vertices
-perturbed by up to 10%.
-
---kernel link times the host link instead (no library call): copies of one
-FP64 E-vector of the nel^3, order-N mesh between pinned host memory and the
-device, host-to-device alone, device-to-host alone and both at once on two
-streams, in GB/s per direction (the ceiling of the end-to-end sem_ax figure).
+perturbed by up to 10%.  --variant selects sem_ax's kernel candidate for the
+order and dtype (see sem_tune_ax; default: the built-in choice).
 """
 from __future__ import annotations
 
 import argparse
 import math
-
-
-def link_bandwidth(n, reps):
-    """GB/s per direction of n-double copies between pinned host memory and
-    cuda:0: host-to-device, device-to-host, and both concurrently."""
-    import torch
-    dev = torch.device("cuda:0")
-    a_h = torch.ones(n, dtype=torch.float64).pin_memory()
-    b_h = torch.empty(n, dtype=torch.float64).pin_memory()
-    a_d = torch.empty(n, dtype=torch.float64, device=dev)
-    b_d = torch.ones(n, dtype=torch.float64, device=dev)
-    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
-
-    def h2d():
-        a_d.copy_(a_h, non_blocking=True)
-
-    def d2h():
-        b_h.copy_(b_d, non_blocking=True)
-
-    def both():
-        cur = torch.cuda.current_stream()
-        s1.wait_stream(cur)
-        s2.wait_stream(cur)
-        with torch.cuda.stream(s1):
-            a_d.copy_(a_h, non_blocking=True)
-        with torch.cuda.stream(s2):
-            b_h.copy_(b_d, non_blocking=True)
-        cur.wait_stream(s1)
-        cur.wait_stream(s2)
-
-    out = {"bytes_per_direction": 8 * n}
-    for name, fn in (("h2d", h2d), ("d2h", d2h), ("both", both)):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        out[name] = {"ms": ms, "GBps_per_direction": 8 * n / ms / 1e6}
-    return out
 
 
 def main(argv=None):
@@ -69,6 +22,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--maxit", type=int, default=20)
     ap.add_argument("--projection", type=int, default=0, help="TGV: pressure projection space")
+    ap.add_argument("--variant", type=int, default=-1, help="sem_ax kernel candidate (-1: default)")
     args = ap.parse_args(argv)
 
     import json
@@ -78,9 +32,6 @@ def main(argv=None):
 
     from . import inputs, sem
     dev = torch.device("cuda:0")
-    if args.kernel == "link":
-        print(json.dumps(link_bandwidth(args.nel ** 3 * (args.N + 1) ** 3, max(args.reps, 3))))
-        return
     nel = (args.nel,) * 3
     tgv = args.kernel.startswith("tgv")
     v = inputs.box_vertices(nel, (2 * math.pi,) * 3, perturb=0.0 if tgv else 0.1)
@@ -88,6 +39,8 @@ def main(argv=None):
     u = torch.from_numpy(inputs.unique_uniform_field(args.N, nel)).to(dev)
     if args.kernel.startswith("ax") or args.kernel == "dssum":
         dt = args.kernel[3:] if args.kernel.startswith("ax") else "f64"
+        if args.variant >= 0:
+            sem.set_ax_variant(args.N, dt, args.variant)
         x = u if dt == "f64" else u.float()
         w = torch.empty_like(x)
         for _ in range(args.reps):
