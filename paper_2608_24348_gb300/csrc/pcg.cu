@@ -18,6 +18,29 @@ SEM_DECL_NP(14) SEM_DECL_NP(15) SEM_DECL_NP(16)
 // Mixed-order kernel for N in {5, 7, 9} (solve_multi.cu), up to 64 problems.
 int sem_solve_launch_multi(const SolveParams<SEM_MAXP> &, int, int, long long, cudaStream_t);
 
+#define SEM_DECL_TAB(NPV) int sem_solve_tables_np##NPV(const void *);
+SEM_DECL_TAB(2) SEM_DECL_TAB(4) SEM_DECL_TAB(6) SEM_DECL_TAB(8) SEM_DECL_TAB(10) SEM_DECL_TAB(12)
+SEM_DECL_TAB(14) SEM_DECL_TAB(16)
+#undef SEM_DECL_TAB
+int sem_solve_tables_multi(int np, const void *tabs);
+
+// Copies the block-floating-point tables of the context's order into the
+// constant memory of the solver kernels that serve it (the per-order unit and,
+// for N + 1 in {6, 8, 10}, the mixed-order unit), on the current device.
+int sem_solve_upload_tables(const sem_ctx *c)
+{
+    if (!c->bfp_tabs) return SEM_OK;  // odd N+1: no such tables
+    typedef int (*tab_fn)(const void *);
+    static const tab_fn f[17] = {nullptr, nullptr, sem_solve_tables_np2, nullptr, sem_solve_tables_np4,
+                                 nullptr, sem_solve_tables_np6, nullptr, sem_solve_tables_np8, nullptr,
+                                 sem_solve_tables_np10, nullptr, sem_solve_tables_np12, nullptr,
+                                 sem_solve_tables_np14, nullptr, sem_solve_tables_np16};
+    if (c->n < 2 || c->n > 16 || !f[c->n]) return SEM_ERR_ARG;
+    int rc = f[c->n](c->bfp_tabs);
+    if (rc == SEM_OK && (c->n == 6 || c->n == 8 || c->n == 10)) rc = sem_solve_tables_multi(c->n, c->bfp_tabs);
+    return rc;
+}
+
 typedef int (*launch8_fn)(const SolveParams<8> &, int, int, long long, cudaStream_t);
 static const launch8_fn k_launch8[17] = {
     nullptr, nullptr, sem_solve_launch_np2, sem_solve_launch_np3, sem_solve_launch_np4,

@@ -311,6 +311,7 @@ extern "C" void sem_destroy(sem_ctx *c)
 
 int sem_solve_state_bytes();             // pcg.cu
 int sem_make_geo_df(sem_ctx *c);         // ax_df.cu
+int sem_solve_upload_tables(const sem_ctx *c);  // pcg.cu
 size_t sem_partials_bytes(int num_sms);  // pcg.cu
 
 extern "C" int sem_setup(int N, int nelx, int nely, int nelz, const double extents[3],
@@ -380,6 +381,8 @@ extern "C" int sem_setup(int N, int nelx, int nely, int nelz, const double exten
     rc = sem_run_geometry(c, nullptr, false, s);
     if (rc != SEM_OK) { sem_destroy(c); return rc; }
     rc = sem_make_geo_df(c);
+    if (rc != SEM_OK) { sem_destroy(c); return rc; }
+    rc = sem_solve_upload_tables(c);
     if (rc != SEM_OK) { sem_destroy(c); return rc; }
     // volume = sum of B
     {

@@ -12,3 +12,5 @@ int sem_solve_launch_multi(const SolveParams<SEM_MAXP> &p, int mode, int sms, lo
         default: return SEM_ERR_ARG;
     }
 }
+
+int sem_solve_tables_multi(int np, const void *tabs) { return solver_upload_bfp_tables(np, tabs); }

@@ -11,3 +11,5 @@ int sem_solve_launch_np8(const SolveParams<8> &p, int mode, int sms, long long m
         default: return SEM_ERR_ARG;
     }
 }
+
+int sem_solve_tables_np8(const void *tabs) { return solver_upload_bfp_tables(8, tabs); }

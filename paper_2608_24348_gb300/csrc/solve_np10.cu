@@ -11,3 +11,5 @@ int sem_solve_launch_np10(const SolveParams<8> &p, int mode, int sms, long long 
         default: return SEM_ERR_ARG;
     }
 }
+
+int sem_solve_tables_np10(const void *tabs) { return solver_upload_bfp_tables(10, tabs); }

@@ -11,3 +11,5 @@ int sem_solve_launch_np16(const SolveParams<8> &p, int mode, int sms, long long 
         default: return SEM_ERR_ARG;
     }
 }
+
+int sem_solve_tables_np16(const void *tabs) { return solver_upload_bfp_tables(16, tabs); }

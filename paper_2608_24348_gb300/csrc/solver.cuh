@@ -41,6 +41,7 @@
 #include <type_traits>
 
 #include "ax.cuh"
+#include "ax_bfp.cuh"
 #include "ax_df.cuh"
 #include "ax_dfeo.cuh"
 #include "ax_tc.cuh"
@@ -64,6 +65,10 @@
 // FP64-accurate element phases of even orders use the folded operator.
 #ifndef SEM_SOLVE_DF_FOLDED
 #define SEM_SOLVE_DF_FOLDED 1
+#endif
+// ... and, for even N+1 <= 12, the block-floating-point operator.
+#ifndef SEM_SOLVE_BFP
+#define SEM_SOLVE_BFP 1
 #endif
 
 // Which element operators a solver kernel carries (keeps each kernel's
@@ -411,6 +416,83 @@ __device__ __forceinline__ void elem_item_dfeo(const ProbDesc &P, double alpha, 
     }
 }
 
+// The block-floating-point operator's tables for each even order, one copy
+// per translation unit (constant-bank operands in the unrolled contractions);
+// filled at context setup, outside any stream capture, by
+// solver_upload_bfp_tables.
+static __constant__ BfpTabs c_bfp_tabs[SEM_NPMAX / 2 + 1];
+
+static inline int solver_upload_bfp_tables(int np, const void *tabs)
+{
+    if (np < 2 || np > SEM_NPMAX || np % 2 || !tabs) return SEM_ERR_ARG;
+    SEM_CUDA(cudaMemcpyToSymbol(c_bfp_tabs, tabs, sizeof(BfpTabs), (size_t)(np / 2) * sizeof(BfpTabs)));
+    return SEM_OK;
+}
+
+// Dynamic shared memory of a block-floating-point element phase: 2 KB of
+// reduction words (zeroed at kernel start; each element leaves them zero),
+// then the slabs.
+#define SEM_BFP_RED_BYTES 2048
+
+template <int NP>
+constexpr bool solve_bfp()
+{
+    return SEM_SOLVE_BFP && BfpCfg<NP>::OK && NP <= 12 && BfpCfg<NP>::THREADS <= SEM_SOLVE_THREADS &&
+           ax_bfp_smem_bytes_ne<NP, BfpCfg<NP>::NE>() + SEM_BFP_RED_BYTES <= 112 * 1024;
+}
+
+
+// FP64-accurate element phases with the block-floating-point operator:
+// kind 0: w = A x;  kind 1: x += alpha p, p = z + beta p, w = A p, <p,w>.
+template <int NP, int KIND>
+__device__ __forceinline__ void elem_item_bfp(const ProbDesc &P, double alpha, double beta, int first,
+                                              int64_t g, unsigned char *smem, double &acc)
+{
+    using C = BfpCfg<NP>;
+    static_assert(8 * C::NE * sizeof(unsigned) <= SEM_BFP_RED_BYTES, "reduction words");
+    unsigned *red = reinterpret_cast<unsigned *>(smem);
+    dfp *slabs = reinterpret_cast<dfp *>(smem + SEM_BFP_RED_BYTES);
+    const int grp = threadIdx.x / C::NP2;
+    const bool inrange = grp < C::NE;
+    // threads beyond the last whole element take part in the barriers only
+    const int tid = inrange ? (int)threadIdx.x - grp * C::NP2 : -1;
+    const int gs = inrange ? grp : 0;
+    const int64_t e = g * C::NE + grp;
+    const bool active = inrange && e < P.E;
+    const int64_t off = (active ? e : 0) * C::NP3;
+    const dfp *geo = P.geodf + (active ? e : 0) * 7 * C::NP3;
+    const float h1h = (float)P.h1, h2h = (float)P.h2;
+    const dfp H1 = {h1h, (float)(P.h1 - (double)h1h)}, H2 = {h2h, (float)(P.h2 - (double)h2h)};
+    geo_prefetch<NP>(P.geodf, g * C::NE, C::NE, P.E, 8);
+    const BfpTabs &T = c_bfp_tabs[NP / 2];
+    dfp *slab = slabs + (size_t)gs * 3 * C::SLAB;
+    if (KIND == 0) {
+        const double *x = P.x + off;
+        double *w = P.w + off;
+        auto load = [&](int q) { return __ldcg(x + q); };
+        auto store = [&](int q, double v) { w[q] = v; };
+        ax_bfp_element<NP, false>(load, store, geo, H1, H2, T, slab, red + gs * 8, tid, active, [] {});
+    } else {
+        const double *r = P.r + off, *mi = P.minv + off;
+        double *p = P.p + off, *w = P.w + off, *x = P.x + off;
+        auto load = [&](int q) {
+            double pn = __ldcg(mi + q) * __ldcg(r + q);
+            if (!first) {
+                const double po = __ldcg(p + q);
+                x[q] = fma(alpha, po, __ldcg(x + q));
+                pn = fma(beta, po, pn);
+            }
+            p[q] = pn;
+            return pn;
+        };
+        auto store = [&](int q, double v) {
+            w[q] = v;
+            acc = fma(__ldcg(p + q), v, acc);
+        };
+        ax_bfp_element<NP, false>(load, store, geo, H1, H2, T, slab, red + gs * 8, tid, active, [] {});
+    }
+}
+
 // FP64-accurate w = A x with the low-register float-pair operator (mixed
 // modes: the FP64 residual of each refinement step); the NE elements of
 // group g one after another.
@@ -461,7 +543,12 @@ __device__ __forceinline__ void elem_dispatch_np(const ProbDesc &P, int ph, doub
                                                  int first, int64_t g, int tc, unsigned char *smem,
                                                  double &acc)
 {
-    if constexpr (MODE == MODE_F64 && df_folded<NP>()) {
+    if constexpr (MODE == MODE_F64 && solve_bfp<NP>()) {
+        if (ph == PH_AX0)
+            elem_item_bfp<NP, 0>(P, alpha, beta, first, g, smem, acc);
+        else
+            elem_item_bfp<NP, 1>(P, alpha, beta, first, g, smem, acc);
+    } else if constexpr (MODE == MODE_F64 && df_folded<NP>()) {
         if (ph == PH_AX0)
             elem_item_dfeo<NP, 0>(P, alpha, beta, first, g, smem, acc);
         else
@@ -882,6 +969,9 @@ __global__ void __launch_bounds__(SEM_SOLVE_THREADS, MODE == MODE_F32 ? SEM_SOLV
     __shared__ unsigned s_gen;
     const int np = prm.nprob;
     SyncState *sync = prm.sync;
+    if constexpr (MODE == MODE_F64)  // reduction words of the block-floating-point element phases
+        for (int t = threadIdx.x; t < SEM_BFP_RED_BYTES / 4; t += blockDim.x)
+            reinterpret_cast<unsigned *>(smem)[t] = 0u;
 
     for (int step = 0;; ++step) {
         // ---- schedule of this step
@@ -1021,7 +1111,8 @@ template <int NP, int MODE>
 constexpr size_t solve_smem_np()
 {
     return MODE == MODE_F64N ? ax_smem_bytes<NP, double>()
-           : MODE == MODE_F64 ? (df_folded<NP>() ? ax_dfeo_smem_bytes<NP>() : ax_df_smem_bytes<NP>())
+           : MODE == MODE_F64 ? (solve_bfp<NP>() ? SEM_BFP_RED_BYTES + ax_bfp_smem_bytes_ne<NP, BfpCfg<NP>::NE>()
+                                 : df_folded<NP>() ? ax_dfeo_smem_bytes<NP>() : ax_df_smem_bytes<NP>())
            : MODE == MODE_F32 ? sem_max_sz(ax_smem_bytes<NP, float>(), ax_df_lowreg_smem_bytes<NP>())
                               : sem_max_sz(ax_tc_smem_bytes<NP>(), ax_df_lowreg_smem_bytes<NP>());
 }
