@@ -122,14 +122,17 @@ def aggregate_gdofs(nodes_per_rank, seconds_max, ws):
     return ws * nodes_per_rank / seconds_max / 1e9
 
 
-def cpu_baseline(seconds=12.0):
-    """The FP64 oracle's operator on the host cores, on a 16^3-element sample of
-    the same deformed N=7 mesh, repeated for about `seconds`."""
+def cpu_baseline(seconds=12.0, threads=None, edge=16):
+    """The FP64 oracle's operator on the host cores, on an edge^3-element sample
+    of the same deformed N=7 mesh, repeated for about `seconds` (threads: the
+    OpenMP thread count, default all cores)."""
     import numpy as np
 
     import oracle
     from paper_2608_24348_gb300 import inputs
-    nel = (16, 16, 16)
+    full = os.cpu_count() or 1
+    oracle.set_threads(threads or full)
+    nel = (edge, edge, edge)
     v = inputs.box_vertices(nel, (2 * math.pi,) * 3, perturb=PERTURB)
     m = oracle.Mesh(N_ORDER, nel, v)
     u = inputs.unique_uniform_field(N_ORDER, nel, seed=inputs.SEED_FIELD)
@@ -140,9 +143,11 @@ def cpu_baseline(seconds=12.0):
         m.ax(u, H1, H2)
         reps += 1
     dt = time.perf_counter() - t0
-    return {"value": m.nL * reps / dt / 1e9, "unit": "GDOF/s", "cores": oracle.threads(),
+    used = oracle.threads()
+    oracle.set_threads(full)
+    return {"value": m.nL * reps / dt / 1e9, "unit": "GDOF/s", "cores": used,
             "kind": "oracle",
-            "sample": f"FP64 oracle sem_ax on a 16^3-element N=7 deformed mesh "
+            "sample": f"FP64 oracle sem_ax on a {edge}^3-element N=7 deformed mesh "
                       f"({m.nL} nodes), {reps} applications in {dt:.1f} s"}, reps, dt
 
 
@@ -240,44 +245,110 @@ def pcg_section(ctx, sem, inputs, stream, ws, reps=1):
     return out
 
 
-def tgv_section(sem, inputs, stream, ws, warm=5, steps=30):
-    """Taylor-Green vortex Re=1600 on 32^3 undeformed elements, N=7, dt=1e-3: the
-    FP64 (A-0) and FP32-compute (A-1) policies of Table 2 with the pressure solve
-    projected onto 20 previous solutions; ms per graph-replayed step (CUDA events
-    around `steps` steps after `warm` steps from the initial state)."""
+def plain_poisson_section(sem, inputs, stream, reps=20):
+    """The plain FP64 Poisson workload: periodic [0, 2 pi]^3, 4x4x4 undeformed
+    elements, N=5, f = 3 sin x sin y sin z (b = dssum(B f), its mean removed by
+    the solver), Jacobi-PCG with the FP64-accurate operator to the relative
+    residual 1e-10 from x0 = 0.  Median of `reps` solves (CUDA events on the
+    launching stream) and the nodal max error against u* = sin x sin y sin z."""
     import torch
-
-    from paper_2608_24348_gb300 import policy
     dev = torch.device("cuda", torch.cuda.current_device())
-    ctx = sem.Ctx(N_ORDER, NEL, (2 * math.pi,) * 3, (1, 1, 1))
+    ctx = sem.Ctx(5, (4, 4, 4), (2 * math.pi,) * 3, (1, 1, 1))
     xyz = torch.empty(3 * ctx.nL, dtype=torch.float64, device=dev)
     ctx.coords(xyz)
     x, y, z = xyz.view(3, -1)
-    ic = [t.contiguous() for t in inputs.tgv_initial(x, y, z, lib=torch)]
-    ic[2] = (ic[2] + 0 * x).contiguous()
-    del xyz
-    out = {"workload": "TGV Re=1600, 32^3 undeformed, N=7, dt=1e-3, projection 20, BDF3/EXT3 with "
-                       "3/2 dealiasing; ms per step after %d start-up steps" % warm}
-    sp = stream.cuda_stream
-    for name in ("A-0", "A-1"):
-        T = sem.TGV(ctx, 1.0 / 1600, 1e-3, vel=sem.opts(tol=1e-6, abs_tol=True),
-                    pres=sem.opts(tol=1e-4, abs_tol=True))
-        T.set_policy([policy.rule(name)])
-        T.set_projection(20)
-        T.set(*ic)
-        T.step(warm, diag=False, stream=stream)
+    us = torch.sin(x) * torch.sin(y) * torch.sin(z)
+    b = torch.empty_like(us)
+    ctx.ax(3.0 * us, b, 0.0, 1.0, "f64", stream=stream.cuda_stream)
+    ctx.dssum(b, "f64", stream=stream.cuda_stream)
+    sol = torch.zeros_like(b)
+    times = []
+    for _ in range(reps):
+        sol.zero_()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        T.step(steps, diag=False, stream=stream)
+        ctx.pcg_solve(b, sol, 1.0, 0.0, sync=False, stream=stream.cuda_stream, tol=1e-10)
         e1.record(stream)
         torch.cuda.synchronize()
-        d = T.step(1, stream=stream)[0]
-        out[name] = {"ms_per_step": barrier_max(e0.elapsed_time(e1) / steps, ws), "ke": d["ke"],
-                     "enstrophy": d["enstrophy"], "iters": d["iters"], "status": d["status"]}
-        T.close()
-    del ic
+        times.append(e0.elapsed_time(e1))
+    info = ctx.last_solve_info()
+    err = float((sol - us).abs().max())
     ctx.close()
+    return {"workload": "plain FP64 Poisson: periodic [0,2pi]^3, 4x4x4 undeformed, N=5, "
+                        "f=3 sin x sin y sin z, rel tol 1e-10", "ms_median": statistics.median(times),
+            "iters": info["iters"], "status": info["status"],
+            "relres": info["rnorm"] / info["bnorm"] if info["bnorm"] else None,
+            "max_err_vs_exact": err}
+
+
+def batched_section(sem, inputs, stream, peak_gbs):
+    """The uneven batch: 64 periodic Poisson problems (E in {8^3 .. 24^3}, N in
+    {5, 7, 9}, sine RHS with seeded wavenumbers) solved in one persistent launch,
+    FP32 inner PCG inside FP64 refinement to 1e-10.  Throughput counts each
+    problem's inner iterations times its local nodes; the HBM fraction counts
+    84 bytes per local node and inner iteration (the FP32 iteration's streams)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    specs = inputs.batch_problems()
+    ctxs, bs, xs = [], [], []
+    for (edge, N, k1, k2, k3) in specs:
+        ctx = sem.Ctx(N, (edge,) * 3, (2 * math.pi,) * 3, (1, 1, 1))
+        xyz = torch.empty(3 * ctx.nL, dtype=torch.float64, device=dev)
+        ctx.coords(xyz)
+        kk = float(k1 * k1 + k2 * k2 + k3 * k3)
+        f = kk * inputs.sine_product((k1, k2, k3), *xyz.view(3, -1), lib=torch)
+        b = torch.empty_like(f)
+        ctx.ax(f, b, 0.0, 1.0, "f64")
+        ctx.dssum(b, "f64")
+        del xyz, f
+        ctxs.append(ctx)
+        bs.append(b)
+        xs.append(torch.zeros_like(b))
+    n = len(ctxs)
+    kw = dict(tol=1e-10, inner="f32", inner_tol=1e-4)
+    sem.pcg_solve_batched(ctxs, bs, xs, [1.0] * n, [0.0] * n, **kw)  # warm-up (Jacobi inverses)
+    for x in xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    # synchronous call: returns once the launch has finished and the infos are filled
+    infos = sem.pcg_solve_batched(ctxs, bs, xs, [1.0] * n, [0.0] * n, stream=stream, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nodes = sum(c.nL for c in ctxs)
+    work = sum(i["iters"] * c.nL for i, c in zip(infos, ctxs))
+    gbs = 84.0 * work / (ms * 1e-3) / 1e9
+    out = {"workload": "64 uneven periodic Poisson problems, E in {8^3..24^3}, N in {5,7,9}, "
+                       "FP32 inner / FP64 refinement to 1e-10, one persistent launch",
+           "ms": ms, "local_nodes": nodes, "inner_iters_total": sum(i["iters"] for i in infos),
+           "status_all_ok": all(i["status"] == 0 for i in infos),
+           "gdofs_iter": work / (ms * 1e-3) / 1e9, "hbm_gbs": gbs, "hbm_frac": gbs / peak_gbs,
+           "tile": {"elements_per_block": {str(N): 256 // (N + 1) ** 2 for N in (5, 7, 9)},
+                    "threads_per_block": 256}}
+    for c in ctxs:
+        c.close()
+    return out
+
+
+def tgv_replay_section(steps=200):
+    """Taylor-Green vortex Re=1600, 32^3 undeformed, N=7, dt=1e-3: 200 steps of the
+    FP64 (A-0) and FP32-compute (A-1) policies of Table 2 from the Sec. 3 initial
+    state, the pressure solve projected onto 20 previous solutions; ms per
+    graph-replayed step (CUDA events around the steps after the first three)
+    and the Sec. 4.2 errors of A-1's KE / enstrophy history against A-0's."""
+    from paper_2608_24348_gb300 import policy
+    rows = policy.replay(configs=["A-0", "A-1"], steps=steps, projection=20)
+    out = {"workload": f"TGV Re=1600, 32^3 undeformed, N=7, dt=1e-3, {steps} steps, projection 20, "
+                       "BDF3/EXT3 with 3/2 dealiasing; ms per graph-replayed step after 3"}
+    for r in rows:
+        out[r["config"]] = {"ms_per_step": r["ms_per_step"], "pres_iters": r["pres_iters"],
+                            "vel_iters": r["vel_iters"], "status": r["status"],
+                            "ke_last": r["ke"][-1], "enstrophy_last": r["enstrophy"][-1],
+                            "e_E_max": r["e_E_max"], "e_Omega_max": r["e_Omega_max"],
+                            "e_Omega_peak": r["e_Omega_peak"]}
     return out
 
 
@@ -328,7 +399,7 @@ def main():
     per_bf, tot_bf = time_kernel(run("bf16_tc", u32, w32), k2, 3, stream, ws)
     per_f16, tot_f16 = time_kernel(run("f16_tc", u32, w32), k2, 3, stream, ws)
     pcg = pcg_section(ctx, sem, inputs, stream, ws)
-    tgv = tgv_section(sem, inputs, stream, ws)
+    plain = plain_poisson_section(sem, inputs, stream)
     clk = clocks.stop()
 
     tot64 = barrier_max(tot64, ws)
@@ -386,14 +457,25 @@ def main():
                   "sem_ax_bf16_tc_gdofs": gdof(barrier_max(tot_bf, ws) / k2),
                   "sem_ax_f16_tc_gdofs": gdof(barrier_max(tot_f16, ws) / k2)},
         "pcg": pcg,
-        "tgv": tgv,
+        "plain_poisson": plain,
         "e2e": {"value": ws * nL / e2e_s / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": 8 * nL,
                 "d2h_bytes_per_step": 8 * nL},
         "gpu_launches": args.steps,
         "clocks": clk,
     }
+    # the batch and the Taylor-Green replay run after the timed operator (their
+    # own CUDA events); the 32^3 context is released first
+    del u64, w64, u32, w32
+    ctx.close()
+    torch.cuda.empty_cache()
+    line["batched"] = batched_section(sem, inputs, stream, pk["hbm_gbs"])
+    torch.cuda.empty_cache()
+    line["tgv"] = tgv_replay_section()
     if rank == 0:
         cb, _, _ = cpu_baseline(seconds=12.0)
+        cb1, _, _ = cpu_baseline(seconds=4.0, threads=1, edge=8)
+        cb["value_1thread"] = cb1["value"]
+        cb["sample_1thread"] = cb1["sample"]
         line["cpu_baseline"] = cb
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -64,6 +64,8 @@ def lib():
             L = ctypes.CDLL(build())
             L.orc_dealias_m.restype = ctypes.c_int
             L.orc_glsc3.restype = ctypes.c_double
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_set_threads.restype = None
             L.orc_glsc3.argtypes = [ctypes.c_long, ctypes.c_int, _dp, _dp, _dp]
             L.orc_ax.argtypes = [ctypes.c_int, ctypes.c_long, _dp, _dp, _dp, ctypes.c_double,
                                  ctypes.c_double, _dp, _dp]
@@ -161,6 +163,11 @@ def fourier(K, cc, cs, x, y, z):
 def threads() -> int:
     """OpenMP threads the oracle uses."""
     return lib().orc_threads()
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of later oracle calls (for timing the baseline)."""
+    lib().orc_set_threads(int(n))
 
 
 def dealias_m(N: int) -> int:

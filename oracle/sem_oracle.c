@@ -58,6 +58,16 @@ int orc_threads(void)
 #endif
 }
 
+/* Sets the OpenMP thread count of later calls (n >= 1; timing only). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* 1-D polynomial tools                                                      */
 /* ------------------------------------------------------------------------ */
