@@ -223,7 +223,9 @@ def pcg_section(ctx, sem, inputs, stream, ws, reps=1):
     sp = stream.cuda_stream
     for name, kw in (("fp64", {}), ("fp64_native", {"inner": "f64_native"}),
                      ("mixed_f32", {"inner": "f32", "inner_tol": 1e-4}),
-                     ("mixed_bf16_tc", {"inner": "bf16_tc", "inner_tol": 1e-2})):
+                     ("mixed_bf16_tc", {"inner": "bf16_tc", "inner_tol": 1e-2}),
+                     ("mixed_f16x2_tc", {"inner": "f16x2_tc", "inner_tol": 1e-4}),
+                     ("mixed_bf16x3_tc", {"inner": "bf16x3_tc", "inner_tol": 1e-4})):
         best = None
         info = None
         for _ in range(reps):
@@ -398,6 +400,8 @@ def main():
     per32, tot32 = time_kernel(run("f32", u32, w32), args.steps, args.warmup, stream, ws)
     per_bf, tot_bf = time_kernel(run("bf16_tc", u32, w32), k2, 3, stream, ws)
     per_f16, tot_f16 = time_kernel(run("f16_tc", u32, w32), k2, 3, stream, ws)
+    _, tot_f16x2 = time_kernel(run("f16x2_tc", u32, w32), k2, 3, stream, ws)
+    _, tot_bf16x3 = time_kernel(run("bf16x3_tc", u32, w32), k2, 3, stream, ws)
     pcg = pcg_section(ctx, sem, inputs, stream, ws)
     plain = plain_poisson_section(sem, inputs, stream)
     clk = clocks.stop()
@@ -455,7 +459,9 @@ def main():
                                "peak": pk["hbm_gbs"], "unit": "GB/s",
                                "frac": hbm(BYTES_F32, avg32) / pk["hbm_gbs"]},
                   "sem_ax_bf16_tc_gdofs": gdof(barrier_max(tot_bf, ws) / k2),
-                  "sem_ax_f16_tc_gdofs": gdof(barrier_max(tot_f16, ws) / k2)},
+                  "sem_ax_f16_tc_gdofs": gdof(barrier_max(tot_f16, ws) / k2),
+                  "sem_ax_f16x2_tc_gdofs": gdof(barrier_max(tot_f16x2, ws) / k2),
+                  "sem_ax_bf16x3_tc_gdofs": gdof(barrier_max(tot_bf16x3, ws) / k2)},
         "pcg": pcg,
         "plain_poisson": plain,
         "e2e": {"value": ws * nL / e2e_s / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": 8 * nL,

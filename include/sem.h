@@ -67,8 +67,17 @@ typedef enum {
     SEM_F32 = 1,       /* FP32 storage and arithmetic */
     SEM_BF16_TC = 2,   /* FP32 storage, BF16 tensor-core contractions, FP32 accumulation */
     SEM_F16_TC = 3,    /* FP32 storage, FP16 tensor-core contractions, FP32 accumulation */
-    SEM_F64_NATIVE = 4 /* FP64 storage, native FP64 FMA arithmetic */
+    SEM_F64_NATIVE = 4, /* FP64 storage, native FP64 FMA arithmetic */
+    SEM_F16X2_TC = 5,   /* FP32 storage, FP16 tensor-core contractions of split operands */
+    SEM_BF16X3_TC = 6   /* FP32 storage, BF16 tensor-core contractions of split operands */
 } sem_dtype;
+/* SEM_F16X2_TC / SEM_BF16X3_TC (N <= 7): every contracted value and D are
+ * split into two FP16 (three BF16) parts, and the tensor cores sum the part
+ * products that carry FP32-level accuracy (about 2^-22) with FP32
+ * accumulation; FP16 parts of an element are first scaled by a power of two
+ * into FP16's range.  As inner operators of refinement they converge where
+ * the plain 16-bit operators (whose error relative to the smallest modes is
+ * the condition number times 2^-8 or 2^-11) do not. */
 /* SEM_F64 in sem_ax evaluates the FP64 operator on the FP32 pipes with
  * error-free transformations (per-element block-floating-point pairs with
  * exact folds and fused exact-product accumulation for odd N <= 11, float

@@ -6,6 +6,8 @@
 
 int sem_ax_tc(sem_ctx *c, const float *u, float *w, double h1, double h2, int fp16,
               cudaStream_t s);  // ax_tc.cu
+int sem_ax_tc_split(sem_ctx *c, const float *u, float *w, double h1, double h2, int fp16,
+                    cudaStream_t s);  // ax_tc.cu
 int sem_launch_ax_f64(const sem_ctx *c, const double *u, double *w, double h1, double h2,
                       cudaStream_t s);  // ax_f64.cu
 int sem_launch_ax_f32_variant(const sem_ctx *c, int variant, const float *u, float *w, float h1,
@@ -86,6 +88,8 @@ int sem_ax_dev(sem_ctx *c, const void *u, void *w, double h1, double h2, sem_dty
                                          (float)h1, (float)h2, s);
     } else if (dt == SEM_BF16_TC || dt == SEM_F16_TC) {
         return sem_ax_tc(c, (const float *)u, (float *)w, h1, h2, dt == SEM_F16_TC, s);
+    } else if (dt == SEM_F16X2_TC || dt == SEM_BF16X3_TC) {
+        return sem_ax_tc_split(c, (const float *)u, (float *)w, h1, h2, dt == SEM_F16X2_TC, s);
     }
     return SEM_ERR_ARG;
 }
@@ -229,7 +233,7 @@ extern "C" int sem_ax(sem_ctx *c, const void *u, void *w, double h1, double h2, 
                       void *stream)
 {
     if (!c || !u || !w) return SEM_ERR_ARG;
-    if (dt < SEM_F64 || dt > SEM_F64_NATIVE) return SEM_ERR_ARG;
+    if (dt < SEM_F64 || dt > SEM_BF16X3_TC) return SEM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const bool uh = !sem_is_device_ptr(u), wh = !sem_is_device_ptr(w);
     if (uh || wh) {
@@ -276,7 +280,7 @@ int sem_dssum_dev(sem_ctx *c, void *u, sem_dtype dt, cudaStream_t s)
 extern "C" int sem_dssum(sem_ctx *c, void *u, sem_dtype dt, void *stream)
 {
     if (!c || !u) return SEM_ERR_ARG;
-    if (dt < SEM_F64 || dt > SEM_F16_TC) return SEM_ERR_ARG;
+    if (dt < SEM_F64 || dt > SEM_BF16X3_TC || dt == SEM_F64_NATIVE) return SEM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     size_t bytes = (size_t)c->nL * (dt == SEM_F64 ? sizeof(double) : sizeof(float));
     const void *ud;

@@ -130,7 +130,10 @@ static void fill_common(SolveParams<MAXP> &p, sem_ctx *owner, const sem_solve_op
 {
     p.nprob = nprob;
     p.mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
-    p.inner_tc = o.inner == SEM_BF16_TC ? 1 : (o.inner == SEM_F16_TC ? 2 : 0);
+    p.inner_tc = o.inner == SEM_BF16_TC ? 1
+                 : o.inner == SEM_F16_TC ? 2
+                 : o.inner == SEM_F16X2_TC ? 3
+                 : o.inner == SEM_BF16X3_TC ? 4 : 0;
     p.abs_tol = o.abs_tol;
     p.maxit = o.maxit;
     p.max_outer = o.max_outer;
@@ -158,7 +161,7 @@ static long long max_items(const ProbDesc *d, int np)
 static int validate_opts(const sem_solve_opts &o)
 {
     if (!(o.tol >= 0) || o.maxit < 0 || o.max_outer < 0) return SEM_ERR_ARG;
-    if (o.inner < SEM_F64 || o.inner > SEM_F64_NATIVE) return SEM_ERR_ARG;
+    if (o.inner < SEM_F64 || o.inner > SEM_BF16X3_TC) return SEM_ERR_ARG;
     const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
     if (mixed && !(o.inner_tol > 0 && o.inner_tol < 1)) return SEM_ERR_ARG;
     return SEM_OK;
@@ -227,8 +230,10 @@ int sem_pcg_solve_dev(sem_ctx *c, int slot, const double *b, double *x, double h
                       const sem_solve_opts &o, cudaStream_t s)
 {
     const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
-    const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC;
-    if (tc && c->n > 10) return SEM_ERR_ARG;
+    const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC || o.inner == SEM_F16X2_TC ||
+                    o.inner == SEM_BF16X3_TC;
+    const int tc_nmax = (o.inner == SEM_F16X2_TC || o.inner == SEM_BF16X3_TC) ? 8 : 10;
+    if (tc && c->n > tc_nmax) return SEM_ERR_ARG;
     ProbDesc d;
     fill_desc(c, c->ws[slot], b, x, h1, h2, mixed, tc, d);
     return jac_forget(c, enqueue(c, o, &d, 1, s));
@@ -242,8 +247,10 @@ int sem_pcg_solve_dev_batch(sem_ctx *c, int np, const double *const *b, double *
     for (int p = 0; p < np; ++p)
         if (!c->ws[slot0 + p].r) return SEM_ERR_ARG;
     const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
-    const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC;
-    if (tc && c->n > 10) return SEM_ERR_ARG;
+    const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC || o.inner == SEM_F16X2_TC ||
+                    o.inner == SEM_BF16X3_TC;
+    const int tc_nmax = (o.inner == SEM_F16X2_TC || o.inner == SEM_BF16X3_TC) ? 8 : 10;
+    if (tc && c->n > tc_nmax) return SEM_ERR_ARG;
     ProbDesc d[8];
     for (int p = 0; p < np; ++p) fill_desc(c, c->ws[slot0 + p], b[p], x[p], h1, h2, mixed, tc, d[p]);
     return jac_forget(c, enqueue(c, o, d, np, s));
@@ -307,7 +314,9 @@ extern "C" int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const doub
     int rc = validate_opts(o);
     if (rc) return rc;
     const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
-    const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC;
+    const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC || o.inner == SEM_F16X2_TC ||
+                    o.inner == SEM_BF16X3_TC;
+    const int tc_nmax = (o.inner == SEM_F16X2_TC || o.inner == SEM_BF16X3_TC) ? 8 : 10;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<ProbDesc> d(nprob);
     std::vector<int> slot(nprob, 0);
@@ -315,7 +324,7 @@ extern "C" int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const doub
         sem_ctx *c = ctxs[p];
         if (!c || !b[p] || !x[p]) return SEM_ERR_ARG;
         if (!(h1[p] >= 0) || !(h2[p] >= 0) || (h1[p] == 0 && h2[p] == 0)) return SEM_ERR_ARG;
-        if (tc && c->n > 10) return SEM_ERR_ARG;
+        if (tc && c->n > tc_nmax) return SEM_ERR_ARG;
         if (!sem_is_device_ptr(b[p]) || !sem_is_device_ptr(x[p])) return SEM_ERR_ARG;
         for (int q = 0; q < p; ++q) slot[p] += (ctxs[q] == c);
         if (slot[p] >= 4) return SEM_ERR_ARG;

@@ -513,10 +513,11 @@ __device__ __forceinline__ void elem_item_lowreg(const ProbDesc &P, int64_t g, u
     }
 }
 
-// TC inner operator (16-bit tensor-core contractions, FP32 vectors).
+// TC inner operator (16-bit tensor-core contractions, FP32 vectors).  tc: 1
+// BF16, 2 FP16 (plain rounding); 3 FP16 x2, 4 BF16 x3 (split operands, N+1 <= 8).
 template <int NP>
 __device__ __forceinline__ void elem_item_tc(const ProbDesc &P, double alpha, double beta, int first,
-                                             int64_t g, int fp16, unsigned char *smem, double &acc)
+                                             int64_t g, int tc, unsigned char *smem, double &acc)
 {
     const float b32 = (float)beta, a32 = (float)alpha;
     auto load = [&](int64_t q) {
@@ -534,7 +535,12 @@ __device__ __forceinline__ void elem_item_tc(const ProbDesc &P, double alpha, do
         P.w32[q] = v;
         dot2_acc(dot, u, v);
     };
-    ax_tc_group<NP>(load, store, P.geo32, P.D32, (float)P.h1, (float)P.h2, P.E, g, fp16, smem);
+    if (tc == 3)
+        ax_tc_split_group<NP, true>(load, store, P.geo32, P.D32, (float)P.h1, (float)P.h2, P.E, g, smem);
+    else if (tc == 4)
+        ax_tc_split_group<NP, false>(load, store, P.geo32, P.D32, (float)P.h1, (float)P.h2, P.E, g, smem);
+    else
+        ax_tc_group<NP>(load, store, P.geo32, P.D32, (float)P.h1, (float)P.h2, P.E, g, tc == 2, smem);
     acc += dfacc_value(dot);
 }
 
@@ -567,7 +573,7 @@ __device__ __forceinline__ void elem_dispatch_np(const ProbDesc &P, int ph, doub
         if (ph == PH_AX0) {
             elem_item_lowreg<NP>(P, g, smem);
         } else if constexpr (MODE == MODE_TC)
-            elem_item_tc<NP>(P, alpha, beta, first, g, tc == 2, smem, acc);
+            elem_item_tc<NP>(P, alpha, beta, first, g, tc, smem, acc);
         else
             elem_item<NP, 2>(P, alpha, beta, first, g, smem, acc);
     }
@@ -1114,7 +1120,8 @@ constexpr size_t solve_smem_np()
            : MODE == MODE_F64 ? (solve_bfp<NP>() ? SEM_BFP_RED_BYTES + ax_bfp_smem_bytes_ne<NP, BfpCfg<NP>::NE>()
                                  : df_folded<NP>() ? ax_dfeo_smem_bytes<NP>() : ax_df_smem_bytes<NP>())
            : MODE == MODE_F32 ? sem_max_sz(ax_smem_bytes<NP, float>(), ax_df_lowreg_smem_bytes<NP>())
-                              : sem_max_sz(ax_tc_smem_bytes<NP>(), ax_df_lowreg_smem_bytes<NP>());
+                              : sem_max_sz(sem_max_sz(ax_tc_smem_bytes<NP>(), ax_tc_split_smem_bytes<NP>()),
+                                           ax_df_lowreg_smem_bytes<NP>());
 }
 
 template <int MODE, int... NPs>

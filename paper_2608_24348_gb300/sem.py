@@ -14,8 +14,9 @@ import threading
 
 from . import build as _build
 
-F64, F32, BF16_TC, F16_TC, F64_NATIVE = 0, 1, 2, 3, 4
-DTYPES = {"f64": F64, "f32": F32, "bf16_tc": BF16_TC, "f16_tc": F16_TC, "f64_native": F64_NATIVE}
+F64, F32, BF16_TC, F16_TC, F64_NATIVE, F16X2_TC, BF16X3_TC = 0, 1, 2, 3, 4, 5, 6
+DTYPES = {"f64": F64, "f32": F32, "bf16_tc": BF16_TC, "f16_tc": F16_TC, "f64_native": F64_NATIVE,
+          "f16x2_tc": F16X2_TC, "bf16x3_tc": BF16X3_TC}
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_BAD_MESH, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT = \
     0, -1, -2, -3, -4, -5, -6, -7

@@ -94,6 +94,40 @@ def test_ax_tensor_core(sem, dtype, bound, N, nel, perturb):
         assert err <= bound, (dtype, N, h1, h2, err)
 
 
+@pytest.mark.parametrize("dtype", ["f16x2_tc", "bf16x3_tc"])
+@pytest.mark.parametrize("N,nel,perturb", [(1, (3, 2, 2), 0.1), (3, (3, 2, 5), 0.1),
+                                           (5, (4, 4, 4), 0.1), (7, (3, 5, 2), 0.1)])
+def test_ax_tensor_core_split_operands(sem, dtype, N, nel, perturb):
+    """Split-operand 16-bit tensor-core contractions reach the FP32 operator's bar
+    (<= 1e-5 of the largest output, on the same FP32-rounded input), on a
+    discontinuous field and on elements scaled by 2^-40 and 2^40 (the FP16 parts
+    are rescaled per element)."""
+    torch, dev = torch_dev()
+    ctx, m, _ = make(sem, N, nel, perturb)
+    u = inputs.local_uniform_field(ctx.nL, seed=7).astype(np.float32)
+    n3 = (N + 1) ** 3
+    us = u.reshape(ctx.E, n3).copy()
+    us[1] *= np.float32(2.0 ** -40)
+    us[2] *= np.float32(2.0 ** 40)
+    for x in (u, us.reshape(-1)):
+        for h1, h2 in ((1.0, 0.0), (0.01, 1000.0)):
+            ref = m.ax(x.astype(np.float64), h1, h2).reshape(ctx.E, n3)
+            ud = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+            wd = torch.empty_like(ud)
+            ctx.ax(ud, wd, h1, h2, dtype)
+            got = wd.cpu().numpy().astype(np.float64).reshape(ctx.E, n3)
+            for e in range(ctx.E):  # each element against its own scale
+                assert rel_err(got[e], ref[e]) <= 1e-5, (dtype, N, h1, h2, e)
+
+
+def test_ax_tensor_core_split_rejects_high_order(sem):
+    torch, dev = torch_dev()
+    ctx, m, _ = make(sem, 8, (1, 1, 1), 0.0)
+    u = torch.zeros(ctx.nL, dtype=torch.float32, device=dev)
+    with pytest.raises(sem.SemError):
+        ctx.ax(u, torch.empty_like(u), 1.0, 0.0, "f16x2_tc")
+
+
 def test_ax_tensor_core_rejects_high_order(sem):
     torch, dev = torch_dev()
     ctx, m, _ = make(sem, 11, (1, 1, 1), 0.0)
