@@ -287,7 +287,8 @@ def plain_poisson_section(sem, inputs, stream, reps=20):
 def batched_section(sem, inputs, stream, peak_gbs):
     """The uneven batch: 64 periodic Poisson problems (E in {8^3 .. 24^3}, N in
     {5, 7, 9}, sine RHS with seeded wavenumbers) solved in one persistent launch,
-    FP32 inner PCG inside FP64 refinement to 1e-10.  Throughput counts each
+    an FP32-accurate inner PCG inside FP64 refinement to 1e-10, each order's
+    inner path (FP32 CUDA cores or split FP16 tensor cores) chosen by the tuner.  Throughput counts each
     problem's inner iterations times its local nodes; the HBM fraction counts
     84 bytes per local node and inner iteration (the FP32 iteration's streams)."""
     import torch
@@ -308,7 +309,13 @@ def batched_section(sem, inputs, stream, peak_gbs):
         bs.append(b)
         xs.append(torch.zeros_like(b))
     n = len(ctxs)
-    kw = dict(tol=1e-10, inner="f32", inner_tol=1e-4)
+    # per-order inner path (FP32 CUDA cores or split FP16 tensor cores) chosen by
+    # the tuner on one context of each order
+    tuned = {}
+    for (edge, N, *_), c in zip(specs, ctxs):
+        if N not in tuned:
+            tuned[N] = sem.tune_inner(c, iters=20)
+    kw = dict(tol=1e-10, inner="f32_tuned", inner_tol=1e-4)
     sem.pcg_solve_batched(ctxs, bs, xs, [1.0] * n, [0.0] * n, **kw)  # warm-up (Jacobi inverses)
     for x in xs:
         x.zero_()
@@ -324,12 +331,16 @@ def batched_section(sem, inputs, stream, peak_gbs):
     work = sum(i["iters"] * c.nL for i, c in zip(infos, ctxs))
     gbs = 84.0 * work / (ms * 1e-3) / 1e9
     out = {"workload": "64 uneven periodic Poisson problems, E in {8^3..24^3}, N in {5,7,9}, "
-                       "FP32 inner / FP64 refinement to 1e-10, one persistent launch",
+                       "FP32-accurate inner (per-order path chosen by the tuner) / FP64 refinement "
+                       "to 1e-10, one persistent launch",
            "ms": ms, "local_nodes": nodes, "inner_iters_total": sum(i["iters"] for i in infos),
            "status_all_ok": all(i["status"] == 0 for i in infos),
            "gdofs_iter": work / (ms * 1e-3) / 1e9, "hbm_gbs": gbs, "hbm_frac": gbs / peak_gbs,
-           "tile": {"elements_per_block": {str(N): 256 // (N + 1) ** 2 for N in (5, 7, 9)},
-                    "threads_per_block": 256}}
+           "tile": {str(N): {"inner_path": "fp16x2_tensor_cores" if t["path"] else "fp32_cuda_cores",
+                             "elements_per_block": 8 if t["path"] else 256 // (N + 1) ** 2,
+                             "ms_per_inner_iter": t["ms_per_iter"]}
+                    for N, t in sorted(tuned.items())},
+           "threads_per_block": 256}
     for c in ctxs:
         c.close()
     return out

@@ -69,7 +69,9 @@ typedef enum {
     SEM_F16_TC = 3,    /* FP32 storage, FP16 tensor-core contractions, FP32 accumulation */
     SEM_F64_NATIVE = 4, /* FP64 storage, native FP64 FMA arithmetic */
     SEM_F16X2_TC = 5,   /* FP32 storage, FP16 tensor-core contractions of split operands */
-    SEM_BF16X3_TC = 6   /* FP32 storage, BF16 tensor-core contractions of split operands */
+    SEM_BF16X3_TC = 6,  /* FP32 storage, BF16 tensor-core contractions of split operands */
+    SEM_F32_TUNED = 7   /* (solver inner operator only) the FP32-accurate inner path chosen per order
+                           by sem_tune_inner; see there */
 } sem_dtype;
 /* SEM_F16X2_TC / SEM_BF16X3_TC (N <= 7): every contracted value and D are
  * split into two FP16 (three BF16) parts, and the tensor cores sum the part
@@ -277,6 +279,24 @@ SEM_API int sem_pcg_solve_noalloc(int N, int nelx, int nely, int nelz, const int
                                   const double *geom, const double *b, double *x, double h1,
                                   double h2, const sem_solve_opts *opts, sem_solve_info *info,
                                   void *stream);
+
+/* Autotuner of the inner path of refinement for the context's order N.  The
+ * candidates are the two FP32-accurate inner operators: 0 = the FP32
+ * CUDA-core operator (256/(N+1)^2 elements per 256-thread block, slabs in
+ * shared memory per element) and 1 = the split-operand FP16 tensor-core
+ * operator (SEM_F16X2_TC: one element per warp, 8 per block; N <= 7 only).
+ * Each runs `iters` inner PCG iterations (a Helmholtz problem on the
+ * context's mesh, one persistent launch) after one untimed run; ms (NULL or
+ * 2 entries) receives the time per inner iteration (-1 where a candidate does
+ * not apply) and *best the faster path, which becomes the order's choice for
+ * solves with inner = SEM_F32_TUNED in this process (and in one batched launch
+ * every problem takes its own order's path).  Allocates two E-vectors for the
+ * run and frees them; synchronous. */
+SEM_API int sem_tune_inner(sem_ctx *ctx, int iters, double *ms, int *best);
+
+/* Sets the inner path of order N for SEM_F32_TUNED (e.g. from a cached tuning
+ * result): 0 FP32 CUDA cores, 1 split FP16 tensor cores (N <= 7). */
+SEM_API int sem_set_inner_path(int N, int path);
 
 /* ---- Taylor-Green vortex stepper (Sec. 3) ---- */
 

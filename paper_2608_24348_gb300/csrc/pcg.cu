@@ -78,15 +78,34 @@ static int ne_for(int n) { return (256 / (n * n)) > 0 ? 256 / (n * n) : 1; }
 // Element groups of the TC path use one warp per element.
 static int TcNE(int n) { return n <= 8 ? 8 : 4; }
 
+// Inner path of SEM_F32_TUNED per order (sem_tune_inner): 0 FP32 CUDA cores,
+// 1 split FP16 tensor cores.
+static int g_inner_path[SEM_NMAX + 1];
+
+// Tensor-core path of a problem of order N (n = N + 1) for an inner dtype: 0
+// = none (FP32 CUDA cores or no inner solve), else ProbDesc::tc.
+static int inner_tc_of(sem_dtype inner, int n)
+{
+    switch (inner) {
+        case SEM_BF16_TC: return 1;
+        case SEM_F16_TC: return 2;
+        case SEM_F16X2_TC: return 3;
+        case SEM_BF16X3_TC: return 4;
+        case SEM_F32_TUNED: return (n - 1 <= SEM_NMAX && g_inner_path[n - 1] == 1 && n <= 8) ? 3 : 0;
+        default: return 0;
+    }
+}
+
 // Fills d for a solve on workspace ws; the Jacobi inverse is recomputed unless
 // ws still holds the one of (h1, h2) (and its FP32 copy when mixed), and ws
 // records what the launch leaves in minv / minv32.
 static void fill_desc(const sem_ctx *c, sem_ws &ws, const double *b, double *x, double h1,
-                      double h2, bool mixed, bool tc, ProbDesc &d)
+                      double h2, bool mixed, int tc, ProbDesc &d)
 {
     memset(&d, 0, sizeof(d));
     d.n = c->n;
     d.NE = ne_for(c->n);
+    d.tc = tc;
     d.NE32 = tc ? TcNE(c->n) : d.NE;
     d.singular = (h2 == 0.0);
     d.E = c->E;
@@ -130,10 +149,7 @@ static void fill_common(SolveParams<MAXP> &p, sem_ctx *owner, const sem_solve_op
 {
     p.nprob = nprob;
     p.mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
-    p.inner_tc = o.inner == SEM_BF16_TC ? 1
-                 : o.inner == SEM_F16_TC ? 2
-                 : o.inner == SEM_F16X2_TC ? 3
-                 : o.inner == SEM_BF16X3_TC ? 4 : 0;
+    p.inner_tc = o.inner == SEM_F32_TUNED ? 0 : inner_tc_of(o.inner, 2);
     p.abs_tol = o.abs_tol;
     p.maxit = o.maxit;
     p.max_outer = o.max_outer;
@@ -161,7 +177,7 @@ static long long max_items(const ProbDesc *d, int np)
 static int validate_opts(const sem_solve_opts &o)
 {
     if (!(o.tol >= 0) || o.maxit < 0 || o.max_outer < 0) return SEM_ERR_ARG;
-    if (o.inner < SEM_F64 || o.inner > SEM_BF16X3_TC) return SEM_ERR_ARG;
+    if (o.inner < SEM_F64 || o.inner > SEM_F32_TUNED) return SEM_ERR_ARG;
     const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
     if (mixed && !(o.inner_tol > 0 && o.inner_tol < 1)) return SEM_ERR_ARG;
     return SEM_OK;
@@ -173,9 +189,11 @@ static int enqueue(sem_ctx *owner, const sem_solve_opts &o, const ProbDesc *d, i
 {
     SEM_CUDA(cudaMemsetAsync(owner->solve_dev, 0, sizeof(SolveStateHost), s));
     const long long mi = max_items(d, np);
+    bool any_tc = false;
+    for (int p = 0; p < np; ++p) any_tc |= (d[p].tc != 0);
     const int mode = o.inner == SEM_F64 ? MODE_F64
                      : o.inner == SEM_F64_NATIVE ? MODE_F64N
-                     : o.inner == SEM_F32 ? MODE_F32 : MODE_TC;
+                     : (o.inner == SEM_F32 || (o.inner == SEM_F32_TUNED && !any_tc)) ? MODE_F32 : MODE_TC;
     bool same = true;
     for (int p = 1; p < np; ++p) same &= (d[p].n == d[0].n);
     int rc;
@@ -231,11 +249,11 @@ int sem_pcg_solve_dev(sem_ctx *c, int slot, const double *b, double *x, double h
 {
     const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
     const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC || o.inner == SEM_F16X2_TC ||
-                    o.inner == SEM_BF16X3_TC;
+                    o.inner == SEM_BF16X3_TC;  // a tensor-core path was asked for
     const int tc_nmax = (o.inner == SEM_F16X2_TC || o.inner == SEM_BF16X3_TC) ? 8 : 10;
     if (tc && c->n > tc_nmax) return SEM_ERR_ARG;
     ProbDesc d;
-    fill_desc(c, c->ws[slot], b, x, h1, h2, mixed, tc, d);
+    fill_desc(c, c->ws[slot], b, x, h1, h2, mixed, inner_tc_of(o.inner, c->n), d);
     return jac_forget(c, enqueue(c, o, &d, 1, s));
 }
 
@@ -248,11 +266,11 @@ int sem_pcg_solve_dev_batch(sem_ctx *c, int np, const double *const *b, double *
         if (!c->ws[slot0 + p].r) return SEM_ERR_ARG;
     const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
     const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC || o.inner == SEM_F16X2_TC ||
-                    o.inner == SEM_BF16X3_TC;
+                    o.inner == SEM_BF16X3_TC;  // a tensor-core path was asked for
     const int tc_nmax = (o.inner == SEM_F16X2_TC || o.inner == SEM_BF16X3_TC) ? 8 : 10;
     if (tc && c->n > tc_nmax) return SEM_ERR_ARG;
     ProbDesc d[8];
-    for (int p = 0; p < np; ++p) fill_desc(c, c->ws[slot0 + p], b[p], x[p], h1, h2, mixed, tc, d[p]);
+    for (int p = 0; p < np; ++p) fill_desc(c, c->ws[slot0 + p], b[p], x[p], h1, h2, mixed, inner_tc_of(o.inner, c->n), d[p]);
     return jac_forget(c, enqueue(c, o, d, np, s));
 }
 
@@ -315,7 +333,7 @@ extern "C" int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const doub
     if (rc) return rc;
     const bool mixed = o.inner != SEM_F64 && o.inner != SEM_F64_NATIVE;
     const bool tc = o.inner == SEM_BF16_TC || o.inner == SEM_F16_TC || o.inner == SEM_F16X2_TC ||
-                    o.inner == SEM_BF16X3_TC;
+                    o.inner == SEM_BF16X3_TC;  // a tensor-core path was asked for
     const int tc_nmax = (o.inner == SEM_F16X2_TC || o.inner == SEM_BF16X3_TC) ? 8 : 10;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<ProbDesc> d(nprob);
@@ -332,7 +350,7 @@ extern "C" int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const doub
             rc = sem_alloc_ws(c, slot[p]);
             if (rc) return rc;
         }
-        fill_desc(c, c->ws[slot[p]], b[p], x[p], h1[p], h2[p], mixed, tc, d[p]);
+        fill_desc(c, c->ws[slot[p]], b[p], x[p], h1[p], h2[p], mixed, inner_tc_of(o.inner, c->n), d[p]);
     }
     sem_ctx *owner = ctxs[0];
     bool multi_ok = true, same = true;
@@ -372,4 +390,78 @@ extern "C" int sem_pcg_solve_batched(int nprob, sem_ctx *const *ctxs, const doub
         }
     }
     return infos ? worst : SEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the inner path (SEM_F32_TUNED)
+// ---------------------------------------------------------------------------
+
+__global__ void k_tune_rhs(double *b, double *x, int64_t n)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    b[q] = (double)((q * 7 + 3) % 11) - 5.0;
+    x[q] = 0.0;
+}
+
+extern "C" int sem_set_inner_path(int N, int path)
+{
+    if (N < 1 || N > SEM_NMAX || path < 0 || path > 1 || (path == 1 && N > 7)) return SEM_ERR_ARG;
+    g_inner_path[N] = path;
+    return SEM_OK;
+}
+
+extern "C" int sem_tune_inner(sem_ctx *c, int iters, double *ms, int *best)
+{
+    if (!c || !best || c->nL == 0) return SEM_ERR_ARG;
+    if (iters < 1) iters = 30;
+    if (ms) ms[0] = ms[1] = -1.0;
+    double *b = nullptr, *x = nullptr;
+    if (cudaMalloc(&b, sizeof(double) * c->nL) != cudaSuccess) return SEM_ERR_NOMEM;
+    if (cudaMalloc(&x, sizeof(double) * c->nL) != cudaSuccess) {
+        cudaFree(b);
+        return SEM_ERR_NOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = SEM_OK;
+    double t[2] = {-1.0, -1.0};
+    const int ncand = c->N <= 7 ? 2 : 1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = SEM_ERR_CUDA;
+    for (int cand = 0; cand < ncand && rc == SEM_OK; ++cand) {
+        // `iters` inner iterations of one refinement step (tolerances out of reach)
+        sem_solve_opts o;
+        sem_solve_opts_default(&o);
+        o.inner = cand == 0 ? SEM_F32 : SEM_F16X2_TC;
+        o.tol = 0.0;
+        o.inner_tol = 1e-30;
+        o.maxit = iters;
+        o.max_outer = 1;
+        float best_ms = 1e30f;
+        for (int rep = 0; rep < 2 && rc == SEM_OK; ++rep) {
+            k_tune_rhs<<<(unsigned)sem_ceil_div(c->nL, 256), 256>>>(b, x, c->nL);
+            if (cudaEventRecord(e0, 0) != cudaSuccess) { rc = SEM_ERR_CUDA; break; }
+            rc = sem_pcg_solve_dev(c, 0, b, x, 1.0, 1.0, o, 0);
+            if (rc) break;
+            if (cudaEventRecord(e1, 0) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = SEM_ERR_CUDA;
+                break;
+            }
+            float f = 0.f;
+            cudaEventElapsedTime(&f, e0, e1);
+            if (rep > 0 && f < best_ms) best_ms = f;  // the first run is a warm-up
+        }
+        if (rc == SEM_OK) t[cand] = best_ms / iters;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(b);
+    cudaFree(x);
+    if (rc) return rc;
+    const int bi = (ncand == 2 && t[1] >= 0 && t[1] < t[0]) ? 1 : 0;
+    if (ms) {
+        ms[0] = t[0];
+        ms[1] = t[1];
+    }
+    *best = bi;
+    return sem_set_inner_path(c->N, bi);
 }

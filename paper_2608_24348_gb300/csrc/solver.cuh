@@ -84,6 +84,8 @@ enum SolvePhase {
 
 struct ProbDesc {
     int n, NE, NE32, singular;  // NE: elements per group (CUDA cores); NE32: inner operator
+    int tc;                     // inner path of a MODE_TC launch: 0 FP32 CUDA cores, 1 BF16, 2 FP16,
+                                // 3 FP16 x2, 4 BF16 x3 tensor cores
     int jac_cached;             // minv (and minv32 if mixed) already hold this problem's Jacobi inverse
     int64_t E, nL, nG;
     GsDesc gs;
@@ -572,9 +574,13 @@ __device__ __forceinline__ void elem_dispatch_np(const ProbDesc &P, int ph, doub
     } else {
         if (ph == PH_AX0) {
             elem_item_lowreg<NP>(P, g, smem);
-        } else if constexpr (MODE == MODE_TC)
-            elem_item_tc<NP>(P, alpha, beta, first, g, tc, smem, acc);
-        else
+        } else if constexpr (MODE == MODE_TC) {
+            // each problem of the launch has its own inner path
+            if (P.tc == 0)
+                elem_item<NP, 2>(P, alpha, beta, first, g, smem, acc);
+            else
+                elem_item_tc<NP>(P, alpha, beta, first, g, P.tc, smem, acc);
+        } else
             elem_item<NP, 2>(P, alpha, beta, first, g, smem, acc);
     }
 }
@@ -1121,7 +1127,7 @@ constexpr size_t solve_smem_np()
                                  : df_folded<NP>() ? ax_dfeo_smem_bytes<NP>() : ax_df_smem_bytes<NP>())
            : MODE == MODE_F32 ? sem_max_sz(ax_smem_bytes<NP, float>(), ax_df_lowreg_smem_bytes<NP>())
                               : sem_max_sz(sem_max_sz(ax_tc_smem_bytes<NP>(), ax_tc_split_smem_bytes<NP>()),
-                                           ax_df_lowreg_smem_bytes<NP>());
+                                           sem_max_sz(ax_df_lowreg_smem_bytes<NP>(), ax_smem_bytes<NP, float>()));
 }
 
 template <int MODE, int... NPs>

@@ -14,9 +14,9 @@ import threading
 
 from . import build as _build
 
-F64, F32, BF16_TC, F16_TC, F64_NATIVE, F16X2_TC, BF16X3_TC = 0, 1, 2, 3, 4, 5, 6
+F64, F32, BF16_TC, F16_TC, F64_NATIVE, F16X2_TC, BF16X3_TC, F32_TUNED = 0, 1, 2, 3, 4, 5, 6, 7
 DTYPES = {"f64": F64, "f32": F32, "bf16_tc": BF16_TC, "f16_tc": F16_TC, "f64_native": F64_NATIVE,
-          "f16x2_tc": F16X2_TC, "bf16x3_tc": BF16X3_TC}
+          "f16x2_tc": F16X2_TC, "bf16x3_tc": BF16X3_TC, "f32_tuned": F32_TUNED}
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_BAD_MESH, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT = \
     0, -1, -2, -3, -4, -5, -6, -7
@@ -72,7 +72,7 @@ EXPORTS = ["sem_setup", "sem_destroy", "sem_get_info", "sem_strerror", "sem_coor
            "sem_last_solve_info", "sem_pcg_solve_batched", "sem_tgv_init", "sem_tgv_set",
            "sem_tgv_step", "sem_tgv_get", "sem_tgv_energy", "sem_tgv_destroy",
            "sem_pcg_solve_noalloc", "sem_device_status", "sem_tune_ax", "sem_set_ax_variant",
-           "sem_tgv_set_policy", "sem_tgv_set_projection"]
+           "sem_tgv_set_policy", "sem_tgv_set_projection", "sem_tune_inner", "sem_set_inner_path"]
 
 
 def lib_path() -> str:
@@ -100,6 +100,8 @@ def load(build_if_missing: bool = True):
         L.sem_device_status.argtypes = [vp]
         L.sem_tune_ax.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, ip]
         L.sem_set_ax_variant.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.sem_tune_inner.argtypes = [vp, ctypes.c_int, dp, ip]
+        L.sem_set_inner_path.argtypes = [ctypes.c_int, ctypes.c_int]
         L.sem_coords.argtypes = [vp, vp, vp]
         L.sem_geom.argtypes = [vp, vp, vp]
         L.sem_ax.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
@@ -330,6 +332,39 @@ def autotune(ctx, dtype="f32", reps=5, cache=None):
     best = ctypes.c_int()
     _check(L.sem_tune_ax(ctx.handle, dt, int(reps), ms, ctypes.byref(best)), "sem_tune_ax")
     out = {"variant": best.value, "ms": [ms[i] for i in range(TUNE_MAX) if ms[i] >= 0]}
+    if cache:
+        table[key] = out
+        os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+        with open(cache, "w") as f:
+            json.dump(table, f, indent=1)
+    return dict(out, cached=False)
+
+
+def set_inner_path(N, path):
+    """Inner path of order N for inner="f32_tuned": 0 FP32 CUDA cores, 1 split FP16 tensor cores."""
+    _check(load().sem_set_inner_path(int(N), int(path)), "sem_set_inner_path")
+
+
+def tune_inner(ctx, iters=30, cache=None):
+    """Pick the inner path of refinement for ctx's order by timing both candidates
+    (sem_tune_inner).  cache: JSON file keyed by (GPU name, N); a cached choice
+    is applied without timing.  Returns {"path": p, "ms_per_iter": [fp32, tc],
+    "cached": bool}."""
+    import json
+    import torch
+    L = load()
+    key = f"{torch.cuda.get_device_name()}|N={ctx.N}|inner"
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+        if key in table:
+            set_inner_path(ctx.N, table[key]["path"])
+            return dict(table[key], cached=True)
+    ms = (ctypes.c_double * 2)(-1.0, -1.0)
+    best = ctypes.c_int()
+    _check(L.sem_tune_inner(ctx.handle, int(iters), ms, ctypes.byref(best)), "sem_tune_inner")
+    out = {"path": best.value, "ms_per_iter": [ms[0], ms[1]]}
     if cache:
         table[key] = out
         os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)

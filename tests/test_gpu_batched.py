@@ -126,3 +126,29 @@ def test_uneven_batch_of_64_in_one_launch(sem):
     full = set(rng.choice(small, size=min(4, len(small)), replace=False).tolist())
     for i in range(64):
         _oracle_check(meta[i], xs[i].cpu().numpy(), full_solve=i in full)
+
+
+def test_tuned_inner_paths_in_one_launch(sem):
+    """inner = f32_tuned: each problem of one launch takes its order's inner path
+    (here N=5 the split FP16 tensor cores, N=7 and N=9 the FP32 CUDA cores), and
+    every residual meets the oracle bar; the tuner times both paths."""
+    specs = [(3, 5, 1, 2, 1), (2, 7, 1, 1, 1), (2, 9, 2, 1, 1), (4, 5, 1, 1, 2)]
+    ctxs, bs, xs, meta = _problems(sem, specs)
+    sem.set_inner_path(5, 1)
+    sem.set_inner_path(7, 0)
+    sem.set_inner_path(9, 0)
+    try:
+        infos = sem.pcg_solve_batched(ctxs, bs, xs, [1.0] * 4, [0.0] * 4, tol=1e-10, inner="f32_tuned",
+                                      inner_tol=1e-4)
+        for i, info in enumerate(infos):
+            assert info["status"] == 0, (meta[i], info)
+            _oracle_check(meta[i], xs[i].cpu().numpy())
+        with pytest.raises(sem.SemError):
+            sem.set_inner_path(9, 1)  # the split tensor-core path serves N <= 7
+        r = sem.tune_inner(ctxs[0], iters=10)
+        assert r["path"] in (0, 1) and r["ms_per_iter"][0] > 0 and r["ms_per_iter"][1] > 0, r
+        r9 = sem.tune_inner(ctxs[2], iters=10)
+        assert r9["path"] == 0 and r9["ms_per_iter"][1] == -1.0, r9
+    finally:
+        for N in (5, 7, 9):
+            sem.set_inner_path(N, 0)
