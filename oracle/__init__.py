@@ -65,6 +65,10 @@ def lib():
             L.orc_dealias_m.restype = ctypes.c_int
             L.orc_glsc3.restype = ctypes.c_double
             L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_cfl.restype = ctypes.c_double
+            L.orc_cfl.argtypes = [ctypes.c_int, ctypes.c_long, _dp, _dp, _dp, _dp, ctypes.c_double]
+            L.orc_bdf_ext_var.argtypes = [ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_double), _dp, _dp]
+            L.orc_tgv_set_dt.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.orc_set_threads.restype = None
             L.orc_glsc3.argtypes = [ctypes.c_long, ctypes.c_int, _dp, _dp, _dp]
             L.orc_ax.argtypes = [ctypes.c_int, ctypes.c_long, _dp, _dp, _dp, ctypes.c_double,
@@ -158,6 +162,20 @@ def fourier(K, cc, cs, x, y, z):
     if rc:
         raise ValueError(f"orc_fourier -> {rc}")
     return out
+
+
+def bdf_ext(q, dts):
+    """Variable-step (b0, b[3], a[3]) of order q for the steps dts = (dt_{n+1}, dt_n, dt_{n-1})."""
+    dts = _f64(list(dts) + [1.0] * (3 - len(dts)))
+    b0 = ctypes.c_double()
+    b, a = np.zeros(3), np.zeros(3)
+    lib().orc_bdf_ext_var(int(q), _p(dts), ctypes.byref(b0), _p(b), _p(a))
+    return b0.value, b, a
+
+
+def cfl(N, E, jinv, u, v, w, dt):
+    """CFL number of (u, v, w) for step dt (reference-space speed over the GLL spacing)."""
+    return lib().orc_cfl(int(N), int(E), _p(_f64(jinv)), _p(_f64(u)), _p(_f64(v)), _p(_f64(w)), float(dt))
 
 
 def threads() -> int:
@@ -305,9 +323,13 @@ class TGV:
         """store32: keep the stored state as FP32 values (rp = fp32, Table 2 group B)."""
         lib().orc_tgv_set_storage(self._h, int(bool(store32)))
 
+    def set_dt(self, dt=0.0, cfl_target=0.0, dt_max=0.0):
+        """Step of the next step (dt > 0) and the adaptive rule (cfl_target > 0)."""
+        lib().orc_tgv_set_dt(self._h, float(dt), float(cfl_target), float(dt_max))
+
     def step(self, nsteps=1):
-        """Advance; returns diag rows {t, KE, enstrophy, it_p, it_u, it_v, it_w, status}."""
-        d = np.zeros((nsteps, 8))
+        """Advance; returns diag rows {t, KE, enstrophy, it_p, it_u, it_v, it_w, status, dt, CFL}."""
+        d = np.zeros((nsteps, 10))
         lib().orc_tgv_step(self._h, nsteps, _p(d))
         return d
 

@@ -815,6 +815,8 @@ typedef struct {
     long E;
     size_t nL;
     double nu, dt, V, t;
+    double hist_dt[2];              /* sizes of the last two steps taken (most recent first) */
+    double cfl_target, dt_max, cfl; /* adaptive step (cfl_target > 0); CFL of the last step */
     double tol_v, tol_p;
     int abs_tol, maxit;
     int step;                       /* steps taken so far */
@@ -826,13 +828,79 @@ typedef struct {
     double *work;                   /* 4 * nL */
 } orc_tgv;
 
-/* BDF / EXT coefficients for order q (textbook, fixed third order: Sec. 3). */
-static void bdf_ext(int q, double *b0, double b[3], double a[3])
+/* BDF / EXT coefficients of order q for variable steps (Sec. 3: fixed third
+ * order; the adaptive CFL step of Sec. 3 makes the steps unequal).  dts[0] is
+ * the step being taken (t^n -> t^{n+1}), dts[1] and dts[2] the two before it.
+ * With tau_0 = t^{n+1}, tau_j = t^{n+1-j} (j = 1..q):
+ *   BDF: u'(tau_0) ~ sum_{j=0..q} l_j'(tau_0) u(tau_j) for the Lagrange basis
+ *        l_j of tau_0..tau_q, written (b0 u^{n+1} - sum_j b_j u^{n+1-j}) / dts[0]:
+ *        b0 = dts[0] l_0'(tau_0), b_j = -dts[0] l_j'(tau_0);
+ *   EXT: u(tau_0) ~ sum_{j=1..q} a_j u(tau_j), a_j = prod_{k=1..q, k!=j}
+ *        (tau_0 - tau_k) / (tau_j - tau_k).
+ * Equal steps give the textbook values (11/6; 3, -3/2, 1/3; 3, -3, 1). */
+void orc_bdf_ext_var(int q, const double *dts, double *b0, double *b, double *a)
 {
+    double tau[4];
+    tau[0] = 0.0;
+    for (int j = 1; j <= 3; ++j) tau[j] = tau[j - 1] - (j <= q ? dts[j - 1] : 1.0);
     b[0] = b[1] = b[2] = a[0] = a[1] = a[2] = 0;
-    if (q == 1) { *b0 = 1.0; b[0] = 1.0; a[0] = 1.0; }
-    else if (q == 2) { *b0 = 1.5; b[0] = 2.0; b[1] = -0.5; a[0] = 2.0; a[1] = -1.0; }
-    else { *b0 = 11.0 / 6.0; b[0] = 3.0; b[1] = -1.5; b[2] = 1.0 / 3.0; a[0] = 3.0; a[1] = -3.0; a[2] = 1.0; }
+    /* l_j'(tau_0) = sum_{m != j} 1/(tau_j - tau_m) prod_{k != j, m} (tau_0 - tau_k)/(tau_j - tau_k) */
+    for (int j = 0; j <= q; ++j) {
+        double d = 0.0;
+        for (int m = 0; m <= q; ++m) {
+            if (m == j) continue;
+            double term = 1.0 / (tau[j] - tau[m]);
+            for (int k = 0; k <= q; ++k)
+                if (k != j && k != m) term *= (tau[0] - tau[k]) / (tau[j] - tau[k]);
+            d += term;
+        }
+        if (j == 0) *b0 = dts[0] * d;
+        else b[j - 1] = -dts[0] * d;
+    }
+    for (int j = 1; j <= q; ++j) {
+        double l = 1.0;
+        for (int k = 1; k <= q; ++k)
+            if (k != j) l *= (tau[0] - tau[k]) / (tau[j] - tau[k]);
+        a[j - 1] = l;
+    }
+}
+
+static void bdf_ext(int q, const double dts[3], double *b0, double b[3], double a[3])
+{
+    orc_bdf_ext_var(q, dts, b0, b, a);
+}
+
+/* CFL number of a velocity field for a step dt (reading of Sec. 3's CFL 0.4):
+ * dt * max over local nodes of sum_a |U_a| / dxi_a, with U_a = sum_c
+ * (dr_a/dx_c) u_c the reference-space velocity and dxi_a the GLL spacing at
+ * the node's index in direction a (the smaller of its two neighbour gaps). */
+double orc_cfl(int N, long E, const double *jinv, const double *u0, const double *u1,
+               const double *u2, double dt)
+{
+    int n = N + 1, n3 = n * n * n;
+    size_t nL = (size_t)E * n3;
+    double xi[ORC_NMAX + 1], w[ORC_NMAX + 1], gap[ORC_NMAX + 1];
+    orc_gll(N, xi, w);
+    for (int i = 0; i <= N; ++i) {
+        double gl = i > 0 ? xi[i] - xi[i - 1] : 1e300, gr = i < N ? xi[i + 1] - xi[i] : 1e300;
+        gap[i] = gl < gr ? gl : gr;
+    }
+    const double *u[3] = {u0, u1, u2};
+    double m = 0.0;
+#pragma omp parallel for reduction(max : m) schedule(static)
+    for (long e = 0; e < E; ++e)
+        for (int p = 0; p < n3; ++p) {
+            size_t q = (size_t)e * n3 + p;
+            int idx[3] = {p % n, (p / n) % n, p / (n * n)};
+            double c = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                double U = 0.0;
+                for (int cc = 0; cc < 3; ++cc) U += jinv[(a * 3 + cc) * nL + q] * u[cc][q];
+                c += fabs(U) / gap[idx[a]];
+            }
+            if (c > m) m = c;
+        }
+    return dt * m;
 }
 
 void *orc_tgv_create(int N, int nelx, int nely, int nelz, const double *vert, const double *L,
@@ -918,7 +986,19 @@ int orc_tgv_set(void *hnd, int h, const double *u0, const double *u1, const doub
         if (p) memcpy(s->p, p, sizeof(double) * s->nL);
         s->step = step;
         s->t = t;
+        s->hist_dt[0] = s->hist_dt[1] = s->dt;  /* earlier levels: steps of the current size */
     }
+    return ORC_OK;
+}
+
+/* Adaptive step (cfl_target > 0; 0 keeps dt fixed) and the step of the next
+ * step (dt > 0; 0 keeps it). */
+int orc_tgv_set_dt(void *hnd, double dt, double cfl_target, double dt_max)
+{
+    orc_tgv *s = hnd;
+    if (dt > 0) s->dt = dt;
+    s->cfl_target = cfl_target > 0 ? cfl_target : 0.0;
+    s->dt_max = dt_max > 0 ? dt_max : 0.0;
     return ORC_OK;
 }
 
@@ -943,7 +1023,8 @@ int orc_tgv_get(void *hnd, double *u0, double *u1, double *u2, double *p)
  *  5. (nu A + (b0/dt) B) u^{n+1}_c = dssum( F_c + B sum_j (b_j/dt) u^{n+1-j}_c
  *                                           - B dp/dx_c ),  PCG from u^n_c,
  *  6. shift histories; diagnostics KE, enstrophy at t^{n+1}.
- * diag[s*8 + ...] = {t, KE, enstrophy, it_p, it_u, it_v, it_w, status}. */
+ * diag[s*10 + ...] = {t, KE, enstrophy, it_p, it_u, it_v, it_w, status, dt of the
+ * step, CFL of the new velocity for that dt}. */
 int orc_tgv_step(void *hnd, int nsteps, double *diag)
 {
     orc_tgv *s = hnd;
@@ -961,8 +1042,9 @@ int orc_tgv_step(void *hnd, int nsteps, double *diag)
     for (int st = 0; st < nsteps; ++st) {
         int q = s->step + 1 < 3 ? s->step + 1 : 3;
         double b0, b[3], a[3];
-        bdf_ext(q, &b0, b, a);
         double dt = s->dt;
+        const double dts[3] = {dt, s->hist_dt[0], s->hist_dt[1]};
+        bdf_ext(q, dts, &b0, b, a);
         /* 1. convective term at level n (C[0] holds it after the previous step's shift) */
         orc_convect(N, s->nelx, s->nely, s->nelz, s->vert, s->jinv, s->u[0][0], s->u[0][1],
                     s->u[0][2], s->C[0][0], s->C[0][1], s->C[0][2]);
@@ -1050,12 +1132,26 @@ int orc_tgv_step(void *hnd, int nsteps, double *diag)
         }
         s->step += 1;
         s->t += dt;
+        s->hist_dt[1] = s->hist_dt[0];
+        s->hist_dt[0] = dt;
         double d[2];
         orc_diag(N, E, s->D, s->jinv, s->B, s->V, s->u[0][0], s->u[0][1], s->u[0][2], d);
+        /* CFL of the new velocity for the step just taken; the adaptive rule
+         * (reading) scales the next step towards the target, by at most +10 %
+         * and -50 % per step, capped by dt_max */
+        s->cfl = orc_cfl(N, E, s->jinv, s->u[0][0], s->u[0][1], s->u[0][2], dt);
+        if (s->cfl_target > 0 && s->cfl > 0) {
+            double f = s->cfl_target / s->cfl;
+            if (f > 1.1) f = 1.1;
+            if (f < 0.5) f = 0.5;
+            s->dt = dt * f;
+            if (s->dt_max > 0 && s->dt > s->dt_max) s->dt = s->dt_max;
+        }
         if (diag) {
-            double *o = diag + 8 * st;
+            double *o = diag + 10 * st;
             o[0] = s->t; o[1] = d[0]; o[2] = d[1];
             o[3] = itp; o[4] = itu[0]; o[5] = itu[1]; o[6] = itu[2]; o[7] = rc_all;
+            o[8] = dt; o[9] = s->cfl;
         }
     }
     for (int c = 0; c < 3; ++c) free(g[c]);

@@ -511,3 +511,145 @@ def test_tgv_fp32_storage_mode():
     assert not np.array_equal(s64, s64.astype(np.float32).astype(np.float64))
     rel = np.abs(d32[:, 1] - d64[:, 1]).max() / np.abs(d64[:, 1]).max()
     assert 0.0 < rel < 1e-6, rel
+
+
+def test_variable_bdf_ext_equal_steps_are_the_textbook_coefficients():
+    """Equal steps: BDF3 (11/6; 3, -3/2, 1/3) and EXT3 (3, -3, 1); BDF2 (3/2; 2, -1/2)."""
+    b0, b, a = oracle.bdf_ext(3, (0.01, 0.01, 0.01))
+    assert abs(b0 - 11 / 6) < 1e-14
+    np.testing.assert_allclose(b, [3.0, -1.5, 1 / 3], atol=1e-13)
+    np.testing.assert_allclose(a, [3.0, -3.0, 1.0], atol=1e-13)
+    b0, b, a = oracle.bdf_ext(2, (0.3, 0.3))
+    assert abs(b0 - 1.5) < 1e-14
+    np.testing.assert_allclose(b, [2.0, -0.5, 0.0], atol=1e-14)
+    np.testing.assert_allclose(a, [2.0, -1.0, 0.0], atol=1e-14)
+    b0, b, a = oracle.bdf_ext(1, (0.7,))
+    assert (b0, b[0], a[0]) == (1.0, 1.0, 1.0)
+
+
+def test_variable_bdf2_closed_form():
+    """Variable-step BDF2: b0 = (1 + 2w)/(1 + w), b1 = (1 + w), b2 = -w^2/(1 + w) with
+    w = dt_{n+1}/dt_n (the textbook variable-step two-step BDF)."""
+    for h0, h1 in ((0.5, 1.0), (1.0, 0.5), (0.013, 0.011)):
+        w = h0 / h1
+        b0, b, a = oracle.bdf_ext(2, (h0, h1))
+        assert abs(b0 - (1 + 2 * w) / (1 + w)) < 1e-13
+        assert abs(b[0] - (1 + w)) < 1e-13
+        assert abs(b[1] + w * w / (1 + w)) < 1e-13
+        np.testing.assert_allclose(a[:2], [1 + w, -w], atol=1e-13)
+
+
+@pytest.mark.parametrize("q", [1, 2, 3])
+def test_variable_bdf_ext_polynomial_exactness(q):
+    """On unequal steps, BDF_q differentiates degree-q polynomials exactly at
+    t_{n+1} and EXT_q extrapolates degree-(q-1) polynomials exactly; one degree
+    more is not exact (the order is q, not more)."""
+    rng = np.random.default_rng(40 + q)
+    for _ in range(5):
+        dts = rng.uniform(0.2, 1.0, 3)
+        t = np.array([0.0, -dts[0], -dts[0] - dts[1], -dts[:3].sum()])
+        b0, b, a = oracle.bdf_ext(q, dts[:q])
+        for deg in range(q + 2):
+            c = rng.standard_normal(deg + 1)
+            f = np.polyval(c, t)
+            df = np.polyval(np.polyder(c), 0.0) if deg else 0.0
+            bdf = (b0 * f[0] - sum(b[j] * f[j + 1] for j in range(q))) / dts[0]
+            ext = sum(a[j] * f[j + 1] for j in range(q))
+            scale = np.abs(c).sum()
+            if deg <= q:
+                assert abs(bdf - df) < 1e-10 * scale / dts[0], (deg, bdf, df)
+            else:
+                assert abs(bdf - df) > 1e-6 * scale
+            if deg <= q - 1:
+                assert abs(ext - f[0]) < 1e-11 * scale
+            elif deg == q:
+                assert abs(ext - f[0]) > 1e-6 * scale
+
+
+def test_cfl_closed_forms_on_a_box():
+    """A uniform velocity on an undeformed box: the CFL number is
+    dt * sum_a |U_a| (2/h_a) / g, with h_a the element width and g the smallest
+    GLL gap (2 at N=1, so dt * sum |U_a|/h_a, the linear-element CFL; 1 at N=2)."""
+    L = (2.0, 3.0, 5.0)
+    nel = (4, 3, 2)
+    U = (0.7, -1.3, 0.2)
+    h = [L[a] / nel[a] for a in range(3)]
+    for N, g in ((1, 2.0), (2, 1.0)):
+        m = mesh(N, nel, 0.0, L=L)
+        uu = [np.full(m.nL, U[a]) for a in range(3)]
+        c = oracle.cfl(N, m.E, m.jinv, *uu, 0.01)
+        ref = 0.01 * sum(abs(U[a]) * 2 / h[a] for a in range(3)) / g
+        assert abs(c - ref) < 1e-13 * ref, (N, c, ref)
+    # N = 4: the smallest GLL gap is 1 - sqrt(3/7)
+    m = mesh(4, nel, 0.0, L=L)
+    c = oracle.cfl(4, m.E, m.jinv, *[np.full(m.nL, U[a]) for a in range(3)], 1.0)
+    ref = sum(abs(U[a]) * 2 / h[a] for a in range(3)) / (1 - math.sqrt(3 / 7))
+    assert abs(c - ref) < 1e-12 * ref
+
+
+def test_cfl_direction_and_location():
+    """Only the node's own velocity counts, and each direction is weighed by the
+    gap at the node's index along it: a velocity at one interior node of N=4
+    (index 2, gaps sqrt(3/7)) gives the CFL of that node alone."""
+    N, nel, L = 4, (2, 2, 2), (2.0, 2.0, 2.0)
+    m = mesh(N, nel, 0.0, L=L)
+    n = N + 1
+    u = [np.zeros(m.nL) for _ in range(3)]
+    q = 3 * n ** 3 + 2 + n * 2 + n * n * 2   # element 3, node (2, 2, 2)
+    u[1][q] = 2.0
+    c = oracle.cfl(N, m.E, m.jinv, *u, 0.5)
+    ref = 0.5 * 2.0 * (2 / 1.0) / math.sqrt(3 / 7)
+    assert abs(c - ref) < 1e-13 * ref
+
+
+def test_tgv_stepper_third_order_with_variable_steps():
+    """Third order survives unequal steps: steps alternating 0.7h, 1.3h (plus a
+    slow drift) on the exact 2-D Taylor-Green vortex converge at rate ~3."""
+    nu, T, N, nel = 0.2, 1.0, 9, (4, 4, 1)
+    v = inputs.box_vertices(nel, (2 * math.pi,) * 3)
+    m = oracle.Mesh(N, nel, v)
+    x, y, z = m.xyz
+    errs = []
+    for h in (0.1, 0.05, 0.025):
+        tgv = oracle.TGV(N, nel, v, (2 * math.pi,) * 3, nu, h, tol_v=1e-13, tol_p=1e-13,
+                         abs_tol=False)
+        for lev in (2, 1, 0):
+            u, vv, w, p = inputs.tg2d_exact(x, y, z, -lev * h, nu)
+            tgv.set(u, vv, w, p if lev == 0 else None, level=lev, step=2, t=0.0)
+        t, k = 0.0, 0
+        while T - t > 1e-12:
+            dt = h * (0.7 if k % 2 == 0 else 1.3) * (1 + 0.1 * math.sin(t))
+            dt = min(dt, T - t)
+            tgv.set_dt(dt)
+            d = tgv.step(1)
+            assert d[0, 7] == 0 and abs(d[0, 8] - dt) < 1e-15
+            t += dt
+            k += 1
+        assert abs(d[0, 0] - T) < 1e-12
+        out = tgv.get()
+        ue, ve, _, _ = inputs.tg2d_exact(x, y, z, T, nu)
+        errs.append(max(np.abs(out[0] - ue).max(), np.abs(out[1] - ve).max()))
+    rates = [math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])]
+    assert rates[0] > 2.6 and rates[1] > 2.6, (errs, rates)
+
+
+def test_tgv_adaptive_step_settles_at_the_target_cfl():
+    """CFL-controlled steps from a step 4x too small: the step grows by at most
+    10 % a step, never past dt_max, and the CFL settles at the target."""
+    N, nel, nu = 5, (3, 3, 3), 1.0 / 1600
+    v = inputs.box_vertices(nel, (2 * math.pi,) * 3)
+    m = oracle.Mesh(N, nel, v)
+    x, y, z = m.xyz
+    tgv = oracle.TGV(N, nel, v, (2 * math.pi,) * 3, nu, 0.01, tol_v=1e-10, tol_p=1e-8,
+                     abs_tol=False)
+    tgv.set(*inputs.tgv_initial(x, y, z))
+    c0 = oracle.cfl(N, m.E, m.jinv, *inputs.tgv_initial(x, y, z)[:3], 0.01)
+    tgv.set_dt(cfl_target=0.4, dt_max=1.0)
+    d = tgv.step(30)
+    assert np.all(d[:, 7] == 0)
+    dts, cfls = d[:, 8], d[:, 9]
+    assert abs(cfls[0] - c0) < 0.02 * c0          # the flow barely moves in one step
+    assert np.all(dts[1:] <= 1.1 * dts[:-1] * (1 + 1e-14))
+    assert np.all(dts <= 1.0)
+    assert abs(cfls[-1] - 0.4) < 0.01, cfls[-5:]
+    np.testing.assert_allclose(np.cumsum(dts), d[:, 0], rtol=1e-13)
