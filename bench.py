@@ -355,13 +355,29 @@ def tgv_replay_section(steps=200):
     from paper_2608_24348_gb300 import policy
     rows = policy.replay(configs=["A-0", "A-1"], steps=steps, projection=20)
     out = {"workload": f"TGV Re=1600, 32^3 undeformed, N=7, dt=1e-3, {steps} steps, projection 20, "
-                       "BDF3/EXT3 with 3/2 dealiasing; ms per graph-replayed step after 3"}
+                       "BDF3/EXT3 with 3/2 dealiasing; ms per graph-replayed step after 3; GPU "
+                       "energy of those steps from NVML's counter"}
     for r in rows:
         out[r["config"]] = {"ms_per_step": r["ms_per_step"], "pres_iters": r["pres_iters"],
                             "vel_iters": r["vel_iters"], "status": r["status"],
                             "ke_last": r["ke"][-1], "enstrophy_last": r["enstrophy"][-1],
                             "e_E_max": r["e_E_max"], "e_Omega_max": r["e_Omega_max"],
-                            "e_Omega_peak": r["e_Omega_peak"]}
+                            "e_Omega_peak": r["e_Omega_peak"], "energy_j": r["energy_j"],
+                            "j_per_step": (r["energy_j"] / (r["steps"] - 3)
+                                           if r["energy_j"] is not None else None)}
+        if r["energy_j"] is None:
+            out[r["config"]]["energy_unavailable"] = r["energy_reason"]
+    # CFL-controlled steps (Sec. 3: CFL 0.4) from the same state: one host
+    # synchronisation and direct launches per step
+    n_cfl = max(20, steps // 2)
+    rows = policy.replay(configs=["A-0", "A-1"], steps=n_cfl, projection=20, cfl=0.4)
+    out["cfl_0.4"] = {"workload": f"the same start, {n_cfl} CFL-controlled steps from dt=1e-3 "
+                                  "(variable-step BDF3/EXT3), ms per step after 3"}
+    for r in rows:
+        out["cfl_0.4"][r["config"]] = {
+            "ms_per_step": r["ms_per_step"], "dt_mean": r.get("dt_mean"), "cfl_mean": r.get("cfl_mean"),
+            "t_end": r.get("t_end"), "pres_iters": r["pres_iters"], "status": r["status"],
+            "e_E_max": r["e_E_max"], "e_Omega_max": r["e_Omega_max"], "energy_j": r["energy_j"]}
     return out
 
 

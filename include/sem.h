@@ -196,6 +196,11 @@ SEM_API int sem_jacobi(sem_ctx *ctx, double h1, double h2, double *minv, void *s
  * inner: the operator precision; SEM_F64 runs plain FP64 PCG, the other three
  * run FP64 iterative refinement around an inner PCG in that precision
  * (vectors FP32, dot products FP64) with relative tolerance inner_tol.
+ * SEM_F64 with a relative tol below 1e-11 runs on the native FP64 operator
+ * (SEM_F64_NATIVE): the FP64-accurate operators on the FP32 pipes carry a
+ * relative error of a few 1e-13 per application, the size of such a residual,
+ * and on a singular periodic Poisson problem their error on the constant
+ * mode can end the solve in SEM_ERR_BREAKDOWN.
  * maxit bounds the PCG iterations (total inner iterations for refinement),
  * max_outer the refinement steps.  wait_timeout_s bounds every device-side
  * wait of the persistent solver (<= 0 selects 10 s); when one runs out the
@@ -304,10 +309,16 @@ typedef struct {
     double t, ke, enstrophy;   /* KE = 1/(2V) sum_local B |u|^2, enstrophy likewise with curl u */
     int iters[4];              /* pressure, u, v, w solver iterations */
     int status;
+    double dt;                 /* size of the step */
+    double cfl;                /* CFL number of the new velocity for that step: dt times the
+                                  largest sum_a |U_a| / dxi_a over the local nodes, U_a =
+                                  sum_c (dr_a/dx_c) u_c, dxi_a the GLL gap at the node's
+                                  index along a (the smaller neighbouring gap) */
 } sem_tgv_diag;
 
 /* Stepper on a periodic context (Sec. 3: the P_N-P_N splitting with BDF3/EXT3
- * and 3/2-rule dealiasing; N <= 9).  nu: viscosity; dt: time step (fixed).
+ * and 3/2-rule dealiasing; N <= 9).  nu: viscosity; dt: time step (fixed
+ * until sem_tgv_set_dt changes it or turns on the CFL-controlled step).
  * op: precision of the dealiased convection: SEM_F64 (FP64-accurate, float
  * pairs on the FP32 pipes), SEM_F64_NATIVE (FP64 arithmetic) or SEM_F32
  * (histories, right-hand sides, refinement residuals and diagnostics stay FP64).  vel / pres: options
@@ -368,6 +379,20 @@ SEM_API int sem_tgv_set_policy(sem_tgv *tgv, int n, const sem_tgv_policy *rules)
  * device; the next step re-captures the step graph.  The basis starts empty. */
 SEM_API int sem_tgv_set_projection(sem_tgv *tgv, int max_vectors);
 
+/* Step size control (Sec. 3: the step adapts to hold CFL = 0.4).  dt > 0 sets
+ * the size of the next step (0 keeps it).  cfl_target > 0 turns on the
+ * CFL-controlled step: after each step the host reads that step's CFL number
+ * (see sem_tgv_diag) and takes the next step dt * f, f = cfl_target / CFL
+ * clamped to [0.5, 1.1], capped by dt_max when dt_max > 0 (a zero CFL keeps the
+ * step); cfl_target = 0 keeps the step fixed.  Unequal steps take the
+ * variable-step BDF3/EXT3 coefficients of the last three step sizes; the
+ * history levels set by sem_tgv_set count as steps of the current size.  A
+ * CFL-controlled run synchronises the stream once per step and launches every
+ * step directly (no graph replay); a changed fixed step re-captures the step
+ * graph once three steps of the new size have run.  SEM_ERR_ARG: NULL tgv or
+ * a negative or NaN argument. */
+SEM_API int sem_tgv_set_dt(sem_tgv *tgv, double dt, double cfl_target, double dt_max);
+
 /* Set the state at history level (0 = u^n, 1 = u^{n-1}, 2 = u^{n-2}) from
  * FP64 E-vectors u, v, w (and p for level 0; may be NULL), each device or host
  * memory (copied); step is the number of steps already taken (selects the
@@ -383,10 +408,11 @@ SEM_API int sem_tgv_set(sem_tgv *tgv, int level, const double *u, const double *
  * returns the first nonzero solve status of those steps
  * (SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN or SEM_ERR_TIMEOUT; the steps still
  * ran, with the last iterate of that solve); without diag the call is
- * stream-ordered and returns SEM_OK or a launch error.  From the third step on
- * each step is one CUDA graph replay (captured on the second steady step after
- * setup or any policy or projection change; direct launches if the capture
- * fails) when stream is not NULL.
+ * stream-ordered and returns SEM_OK or a launch error (a CFL-controlled run
+ * synchronises once per step).  With a fixed step, from the third step of one
+ * size on each step is one CUDA graph replay (captured on the second such step
+ * after setup or any policy, projection or step-size change; direct launches
+ * if the capture fails) when stream is not NULL.
  * SEM_ERR_ARG: NULL tgv or nsteps < 0. */
 SEM_API int sem_tgv_step(sem_tgv *tgv, int nsteps, sem_tgv_diag *diag, void *stream);
 

@@ -191,7 +191,14 @@ static int enqueue(sem_ctx *owner, const sem_solve_opts &o, const ProbDesc *d, i
     const long long mi = max_items(d, np);
     bool any_tc = false;
     for (int p = 0; p < np; ++p) any_tc |= (d[p].tc != 0);
-    const int mode = o.inner == SEM_F64 ? MODE_F64
+    // Plain FP64 PCG to a relative tolerance below 1e-11 runs on the native
+    // FP64 operator: the float-pair and block-floating-point operators of
+    // SEM_F64 carry a relative error of a few 1e-13 per application, the size
+    // of such a residual, and on a singular (periodic Poisson) problem their
+    // error on the constant mode can end the solve with <p,Ap> <= 0.
+    const bool tight = o.inner == SEM_F64 && !o.abs_tol && o.tol < 1e-11;
+    const int mode = tight ? MODE_F64N
+                     : o.inner == SEM_F64 ? MODE_F64
                      : o.inner == SEM_F64_NATIVE ? MODE_F64N
                      : (o.inner == SEM_F32 || (o.inner == SEM_F32_TUNED && !any_tc)) ? MODE_F32 : MODE_TC;
     bool same = true;

@@ -52,11 +52,13 @@ struct TgvLogEntry {
     int iters[4];
     int status;
     int pad;
+    double dt, cfl;   // the step's size and the CFL number of its new velocity
 };
 
 struct TgvDev {       // device-side counters
     long long count;  // entries written so far
     double t;
+    double cfl;       // CFL number of the latest step
 };
 
 struct sem_tgv {
@@ -77,6 +79,9 @@ struct sem_tgv {
     int *pint;             // device ints: basis size L, 1, restart flag
     int step, M;
     double t;
+    double hist_dt[2];        // sizes of the last two steps (most recent first)
+    double cfl_target, dt_max; // adaptive step when cfl_target > 0
+    TgvDev *hdev;             // pinned host copy of the counters
     double *u[3][3], *C[3][3], *p, *unew[3], *F[3], *g[3], *bp, *rhs[3];
     double *part;      // [E][2]
     double *tab64;     // eta[M], wq[M], J[M*n]
@@ -509,14 +514,21 @@ __global__ void k_tgv_vrhs(VArgs a)
 // Per-element sum of B|u|^2 and B|curl u|^2.
 // T as in k_tgv_divg: the gradients, the vorticity and both integrals per
 // element in T; the block sums in FP64.
+// With them, the element's largest sum_a |U_a| / dxi_a over its nodes (U_a =
+// sum_c (dr_a/dx_c) u_c, dxi_a the GLL gap at the node's index along a; the
+// CFL number per unit step, Sec. 3), in FP64 from the T-accurate U_a.
+struct GapInv {
+    double v[SEM_NPMAX];
+};
+
 template <int NP, typename T>
 __global__ void k_tgv_diag_part(const double *u0, const double *u1, const double *u2,
-                                const T *jinv, const T *geo, const T *D, double *part, int64_t E)
+                                const T *jinv, const T *geo, const T *D, GapInv ig, double *part, int64_t E)
 {
     constexpr int N3 = NP * NP * NP;
     __shared__ T su[3 * N3];
     __shared__ T sD[NP * NP];
-    __shared__ double sred[2 * 32];
+    __shared__ double sred[3 * 32];
     for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sD[t] = D[t];
     const double *uu[3] = {u0, u1, u2};
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
@@ -525,9 +537,21 @@ __global__ void k_tgv_diag_part(const double *u0, const double *u1, const double
         for (int t = threadIdx.x; t < 3 * N3; t += blockDim.x) su[t] = T(uu[t / N3][off + t % N3]);
         __syncthreads();
         T tke = 0, ten = 0;
+        double cmax = 0.0;
         for (int pn = threadIdx.x; pn < N3; pn += blockDim.x) {
             const int i = pn % NP, j = (pn / NP) % NP, k = pn / (NP * NP);
             const T *ji = jinv + e * 9 * N3 + pn;
+            {
+                const int ia[3] = {i, j, k};
+                double cn = 0.0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const T U = fma(ji[(a * 3 + 0) * N3], su[pn],
+                                    fma(ji[(a * 3 + 1) * N3], su[N3 + pn], ji[(a * 3 + 2) * N3] * su[2 * N3 + pn]));
+                    cn += fabs((double)U) * ig.v[ia[a]];
+                }
+                cmax = fmax(cmax, cn);
+            }
             T du[3][3];  // du[c][d] = du_c / dx_d
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -552,41 +576,49 @@ __global__ void k_tgv_diag_part(const double *u0, const double *u1, const double
         for (int o = 16; o > 0; o >>= 1) {
             ke += __shfl_xor_sync(0xffffffffu, ke, o);
             en += __shfl_xor_sync(0xffffffffu, en, o);
+            cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
         }
         if ((threadIdx.x & 31) == 0) {
-            sred[2 * (threadIdx.x >> 5)] = ke;
-            sred[2 * (threadIdx.x >> 5) + 1] = en;
+            sred[3 * (threadIdx.x >> 5)] = ke;
+            sred[3 * (threadIdx.x >> 5) + 1] = en;
+            sred[3 * (threadIdx.x >> 5) + 2] = cmax;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double a = 0, b = 0;
+            double a = 0, b = 0, m = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                a += sred[2 * w];
-                b += sred[2 * w + 1];
+                a += sred[3 * w];
+                b += sred[3 * w + 1];
+                m = fmax(m, sred[3 * w + 2]);
             }
-            part[2 * e] = a;
-            part[2 * e + 1] = b;
+            part[3 * e] = a;
+            part[3 * e + 1] = b;
+            part[3 * e + 2] = m;
         }
     }
 }
 
-// Fixed-order sum of the element partials into the log; advances time and count.
+// Fixed-order sum of the element partials into the log (and the largest CFL
+// rate times dt); advances time and count.
 __global__ void k_tgv_diag_final(const double *part, int64_t E, double V, double dt, TgvDev *dv,
                                  TgvLogEntry *log, int advance)
 {
-    __shared__ double s[2][256];
-    double a = 0.0, b = 0.0;
+    __shared__ double s[3][256];
+    double a = 0.0, b = 0.0, m = 0.0;
     for (int64_t e = threadIdx.x; e < E; e += blockDim.x) {
-        a += part[2 * e];
-        b += part[2 * e + 1];
+        a += part[3 * e];
+        b += part[3 * e + 1];
+        m = fmax(m, part[3 * e + 2]);
     }
     s[0][threadIdx.x] = a;
     s[1][threadIdx.x] = b;
+    s[2][threadIdx.x] = m;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
             s[0][threadIdx.x] += s[0][threadIdx.x + o];
             s[1][threadIdx.x] += s[1][threadIdx.x + o];
+            s[2][threadIdx.x] = fmax(s[2][threadIdx.x], s[2][threadIdx.x + o]);
         }
         __syncthreads();
     }
@@ -596,7 +628,12 @@ __global__ void k_tgv_diag_final(const double *part, int64_t E, double V, double
         L.t = dv->t;
         L.ke = s[0][0] / (2.0 * V);
         L.en = s[1][0] / (2.0 * V);
-        if (advance) dv->count += 1;
+        L.dt = dt;
+        L.cfl = dt * s[2][0];
+        if (advance) {
+            dv->cfl = L.cfl;
+            dv->count += 1;
+        }
     }
 }
 
@@ -719,15 +756,57 @@ static int convect(sem_tgv *T, const double *const u[3], double *const C[3], cud
     return SEM_ERR_ARG;
 }
 
-static Coef coef(int q, double dt)
+// BDF_q / EXT_q coefficients for the step h0 = t^{n+1} - t^n after steps h1,
+// h2 (Sec. 3; unequal under the CFL-controlled step).  With the distances
+// s1 = h0, s2 = h0 + h1, s3 = s2 + h2 from t^{n+1} back to the earlier levels,
+// differentiating and extrapolating the interpolant through those levels gives
+//   q = 3: b0 = h0 (1/s1 + 1/s2 + 1/s3), b1 = s2 s3 / (h1 (h1 + h2)),
+//          b2 = -h0^2 s3 / (s2 h1 h2), b3 = h0^2 s2 / (s3 (h1 + h2) h2),
+//          a1 = s2 s3 / (h1 (h1 + h2)), a2 = -s1 s3 / (h1 h2), a3 = s1 s2 / ((h1 + h2) h2);
+//   q = 2: b0 = h0 (1/s1 + 1/s2), b1 = s2 / h1, b2 = -h0^2 / (s2 h1),
+//          a1 = s2 / h1, a2 = -s1 / h1;
+//   q = 1: b0 = b1 = a1 = 1.
+// Equal steps take the textbook constants exactly (11/6; 3, -3/2, 1/3; 3, -3, 1).
+static Coef coef(int q, double h0, double h1, double h2)
 {
     Coef k;
     memset(&k, 0, sizeof(k));
-    k.dt = dt;
+    k.dt = h0;
+    const bool equal = h1 == h0 && (q < 3 || h2 == h0);
     if (q == 1) { k.b0 = 1.0; k.b[0] = 1.0; k.a[0] = 1.0; }
-    else if (q == 2) { k.b0 = 1.5; k.b[0] = 2.0; k.b[1] = -0.5; k.a[0] = 2.0; k.a[1] = -1.0; }
-    else { k.b0 = 11.0 / 6.0; k.b[0] = 3.0; k.b[1] = -1.5; k.b[2] = 1.0 / 3.0; k.a[0] = 3.0; k.a[1] = -3.0; k.a[2] = 1.0; }
+    else if (q == 2 && equal) { k.b0 = 1.5; k.b[0] = 2.0; k.b[1] = -0.5; k.a[0] = 2.0; k.a[1] = -1.0; }
+    else if (equal) { k.b0 = 11.0 / 6.0; k.b[0] = 3.0; k.b[1] = -1.5; k.b[2] = 1.0 / 3.0; k.a[0] = 3.0; k.a[1] = -3.0; k.a[2] = 1.0; }
+    else if (q == 2) {
+        const double s1 = h0, s2 = h0 + h1;
+        k.b0 = h0 * (1.0 / s1 + 1.0 / s2);
+        k.b[0] = s2 / h1;
+        k.b[1] = -h0 * h0 / (s2 * h1);
+        k.a[0] = s2 / h1;
+        k.a[1] = -s1 / h1;
+    } else {
+        const double s1 = h0, s2 = h0 + h1, s3 = s2 + h2, h12 = h1 + h2;
+        k.b0 = h0 * (1.0 / s1 + 1.0 / s2 + 1.0 / s3);
+        k.b[0] = s2 * s3 / (h1 * h12);
+        k.b[1] = -h0 * h0 * s3 / (s2 * h1 * h2);
+        k.b[2] = h0 * h0 * s2 / (s3 * h12 * h2);
+        k.a[0] = s2 * s3 / (h1 * h12);
+        k.a[1] = -s1 * s3 / (h1 * h2);
+        k.a[2] = s1 * s2 / (h12 * h2);
+    }
     return k;
+}
+
+static GapInv gap_inv(const sem_ctx *c)
+{
+    GapInv g;
+    memset(&g, 0, sizeof(g));
+    const int N = c->n - 1;
+    for (int i = 0; i <= N; ++i) {
+        const double l = i > 0 ? c->hxi[i] - c->hxi[i - 1] : 1e300;
+        const double r = i < N ? c->hxi[i + 1] - c->hxi[i] : 1e300;
+        g.v[i] = 1.0 / (l < r ? l : r);
+    }
+    return g;
 }
 
 static int diag(sem_tgv *T, int advance, cudaStream_t s)
@@ -737,7 +816,7 @@ static int diag(sem_tgv *T, int advance, cudaStream_t s)
     // FP64-accurate on the FP32 pipes (J^-1, B and D as float pairs)
     TGV_DISPATCH(c->n, k_tgv_diag_part<NP, df64><<<blocks, 256, 0, s>>>(
                            T->u[0][0], T->u[0][1], T->u[0][2], T->jinvdf, (const df64 *)c->geodf,
-                           (const df64 *)c->tabdf, T->part, c->E));
+                           (const df64 *)c->tabdf, gap_inv(c), T->part, c->E));
     SEM_CHECK_LAUNCH();
     const double V = c->volume;
     k_tgv_diag_final<<<1, 256, 0, s>>>(T->part, c->E, V, T->dt, T->dev, T->log, advance);
@@ -754,7 +833,7 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     sem_ctx *c = T->c;
     const int64_t nL = c->nL;
     const size_t bytes = sizeof(double) * nL;
-    const Coef k = coef(q, T->dt);
+    const Coef k = coef(q, T->dt, T->hist_dt[0], T->hist_dt[1]);
     int rc;
     // 1. convective term of the current velocity (stored: C history)
     rc = convect(T, T->u[0], T->C[0], s);
@@ -852,6 +931,7 @@ extern "C" void sem_tgv_destroy(sem_tgv *T)
     if (T->log) cudaFree(T->log);
     if (T->dev) cudaFree(T->dev);
     if (T->hlog) cudaFreeHost(T->hlog);
+    if (T->hdev) cudaFreeHost(T->hdev);
     free(T);
 }
 
@@ -868,6 +948,7 @@ extern "C" int sem_tgv_init(sem_ctx *c, double nu, double dt, sem_dtype op, cons
     T->c = c;
     T->nu = nu;
     T->dt = dt;
+    T->hist_dt[0] = T->hist_dt[1] = dt;
     T->op = op;
     sem_solve_opts_default(&T->vo);
     sem_solve_opts_default(&T->po);
@@ -905,7 +986,7 @@ extern "C" int sem_tgv_init(sem_ctx *c, double nu, double dt, sem_dtype op, cons
     for (int k = 0; k < 3; ++k) { T->g[k] = b; b += nL; }
     T->bp = b; b += nL;
     for (int k = 0; k < 3; ++k) { T->rhs[k] = b; b += nL; }
-    TGV_TRY(cudaMalloc(&T->part, sizeof(double) * 2 * c->E));
+    TGV_TRY(cudaMalloc(&T->part, sizeof(double) * 3 * c->E));
     // dealiasing tables
     double eta[64], wq[64], J[64 * SEM_NPMAX], h64[2 * 64 + 64 * SEM_NPMAX];
     float h32[2 * 64 + 64 * SEM_NPMAX];
@@ -931,6 +1012,7 @@ extern "C" int sem_tgv_init(sem_ctx *c, double nu, double dt, sem_dtype op, cons
     TGV_TRY(cudaMalloc(&T->log, sizeof(TgvLogEntry) * TGV_LOG));
     TGV_TRY(cudaMemset(T->log, 0, sizeof(TgvLogEntry) * TGV_LOG));
     TGV_TRY(cudaMallocHost(&T->hlog, sizeof(TgvLogEntry) * TGV_LOG));
+    TGV_TRY(cudaMallocHost(&T->hdev, sizeof(TgvDev)));
     TGV_TRY(cudaMalloc(&T->dev, sizeof(TgvDev)));
     TGV_TRY(cudaMemset(T->dev, 0, sizeof(TgvDev)));
     // J^{-1} on the context and three solver workspaces for the velocity batch
@@ -985,6 +1067,7 @@ extern "C" int sem_tgv_set(sem_tgv *T, int level, const double *u, const double 
     if (level == 0) {
         T->step = step;
         T->t = t;
+        T->hist_dt[0] = T->hist_dt[1] = T->dt;  // earlier levels: steps of the current size
         k_tgv_set_time<<<1, 1, 0, s>>>(T->dev, t);
         SEM_CHECK_LAUNCH();
     }
@@ -1296,14 +1379,17 @@ static int advance(sem_tgv *T, int nsteps, cudaStream_t s)
 {
     for (int it = 0; it < nsteps; ++it) {
         const int q = T->step + 1 < 3 ? T->step + 1 : 3;
+        const bool adaptive = T->cfl_target > 0;
+        // graph replay only for third-order steps of one fixed size
+        const bool steady = q == 3 && !adaptive && T->hist_dt[0] == T->dt && T->hist_dt[1] == T->dt;
         int rc;
         apply_policy(T, T->step + 1);
-        if (q == 3 && s != 0 && T->graph_state == 0 && !T->graph_warm) {
+        if (steady && s != 0 && T->graph_state == 0 && !T->graph_warm) {
             // one steady step runs directly first, so the Jacobi inverses of its
             // solves are cached when the next one is captured (the graph then
             // keeps reusing them)
             T->graph_warm = 1;
-        } else if (q == 3 && s != 0 && T->graph_state == 0) {
+        } else if (steady && s != 0 && T->graph_state == 0) {
             // capture one steady-state step; fall back to direct launches if capture fails
             cudaGraph_t g = nullptr;
             T->graph_state = -1;
@@ -1319,7 +1405,7 @@ static int advance(sem_tgv *T, int nsteps, cudaStream_t s)
             }
             cudaGetLastError();
         }
-        if (q == 3 && T->graph_state == 1) {
+        if (steady && T->graph_state == 1) {
             SEM_CUDA(cudaGraphLaunch(T->graph, s));
         } else {
             rc = step_once(T, q, s);
@@ -1327,7 +1413,38 @@ static int advance(sem_tgv *T, int nsteps, cudaStream_t s)
         }
         T->step += 1;
         T->t += T->dt;
+        T->hist_dt[1] = T->hist_dt[0];
+        T->hist_dt[0] = T->dt;
+        if (adaptive) {
+            // next step from this step's CFL number: towards the target, by at
+            // most +10 % and -50 % a step, capped by dt_max (a zero or NaN CFL
+            // keeps the step)
+            SEM_CUDA(cudaMemcpyAsync(T->hdev, T->dev, sizeof(TgvDev), cudaMemcpyDeviceToHost, s));
+            SEM_CUDA(cudaStreamSynchronize(s));
+            const double cfl = T->hdev->cfl;
+            if (cfl > 0) {
+                double f = T->cfl_target / cfl;
+                if (f > 1.1) f = 1.1;
+                if (f < 0.5) f = 0.5;
+                T->dt = T->dt * f;
+                if (T->dt_max > 0 && T->dt > T->dt_max) T->dt = T->dt_max;
+            }
+        }
     }
+    return SEM_OK;
+}
+
+extern "C" int sem_tgv_set_dt(sem_tgv *T, double dt, double cfl_target, double dt_max)
+{
+    if (!T || !(dt >= 0) || !(cfl_target >= 0) || !(dt_max >= 0)) return SEM_ERR_ARG;
+    if (dt > 0) T->dt = dt;
+    T->cfl_target = cfl_target;
+    T->dt_max = dt_max;
+    if (T->graph_state == 1 && (dt > 0 || cfl_target > 0)) {  // the graph holds the old step's coefficients
+        cudaGraphExecDestroy(T->graph);
+        T->graph_state = 0;
+    }
+    if (dt > 0 || cfl_target > 0) T->graph_warm = 0;
     return SEM_OK;
 }
 
@@ -1356,6 +1473,8 @@ extern "C" int sem_tgv_step(sem_tgv *T, int nsteps, sem_tgv_diag *out, void *str
             D.enstrophy = L.en;
             for (int k = 0; k < 4; ++k) D.iters[k] = L.iters[k];
             D.status = L.status;
+            D.dt = L.dt;
+            D.cfl = L.cfl;
             if (L.status != 0 && worst == SEM_OK) worst = L.status;
         }
         done += n;

@@ -64,7 +64,8 @@ class TgvPolicy(ctypes.Structure):
 
 class TgvDiag(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("ke", ctypes.c_double), ("enstrophy", ctypes.c_double),
-                ("iters", ctypes.c_int * 4), ("status", ctypes.c_int)]
+                ("iters", ctypes.c_int * 4), ("status", ctypes.c_int), ("dt", ctypes.c_double),
+                ("cfl", ctypes.c_double)]
 
 
 EXPORTS = ["sem_setup", "sem_destroy", "sem_get_info", "sem_strerror", "sem_coords", "sem_geom",
@@ -72,7 +73,8 @@ EXPORTS = ["sem_setup", "sem_destroy", "sem_get_info", "sem_strerror", "sem_coor
            "sem_last_solve_info", "sem_pcg_solve_batched", "sem_tgv_init", "sem_tgv_set",
            "sem_tgv_step", "sem_tgv_get", "sem_tgv_energy", "sem_tgv_destroy",
            "sem_pcg_solve_noalloc", "sem_device_status", "sem_tune_ax", "sem_set_ax_variant",
-           "sem_tgv_set_policy", "sem_tgv_set_projection", "sem_tune_inner", "sem_set_inner_path"]
+           "sem_tgv_set_policy", "sem_tgv_set_projection", "sem_tune_inner", "sem_set_inner_path",
+           "sem_tgv_set_dt"]
 
 
 def lib_path() -> str:
@@ -125,6 +127,7 @@ def load(build_if_missing: bool = True):
         L.sem_tgv_destroy.argtypes = [vp]
         L.sem_tgv_set_policy.argtypes = [vp, ctypes.c_int, ctypes.POINTER(TgvPolicy)]
         L.sem_tgv_set_projection.argtypes = [vp, ctypes.c_int]
+        L.sem_tgv_set_dt.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.sem_tgv_destroy.restype = None
         L.sem_pcg_solve_noalloc.argtypes = [ctypes.c_int] * 4 + [ip, vp, vp, vp, ctypes.c_double,
                                                                  ctypes.c_double,
@@ -401,6 +404,13 @@ class TGV:
         """Keep up to max_vectors earlier pressure solutions for projection (0 = off)."""
         _check(_lib.sem_tgv_set_projection(self._h, int(max_vectors)), "sem_tgv_set_projection")
 
+    def set_dt(self, dt=0.0, cfl_target=0.0, dt_max=0.0):
+        """Size of the next step (dt > 0) and the CFL-controlled step
+        (cfl_target > 0: each next step from the last step's CFL number, capped
+        by dt_max > 0; 0 keeps the step fixed)."""
+        _check(_lib.sem_tgv_set_dt(self._h, float(dt), float(cfl_target), float(dt_max)),
+               "sem_tgv_set_dt")
+
     def set(self, u, v, w, p=None, level=0, step=0, t=0.0, stream=None):
         _check(_lib.sem_tgv_set(self._h, level, ptr(u), ptr(v), ptr(w), ptr(p), step, t,
                                 _sp(u, stream)), "sem_tgv_set")
@@ -414,7 +424,7 @@ class TGV:
             if rc not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT):
                 _check(rc, "sem_tgv_step")
             return [{"t": x.t, "ke": x.ke, "enstrophy": x.enstrophy, "iters": list(x.iters),
-                     "status": x.status} for x in d]
+                     "status": x.status, "dt": x.dt, "cfl": x.cfl} for x in d]
         _check(_lib.sem_tgv_step(self._h, nsteps, None, sp), "sem_tgv_step")
         return None
 

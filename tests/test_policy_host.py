@@ -110,6 +110,24 @@ class _FakeStream:
         pass
 
 
+class _FakeMeter:
+    """EnergyMeter stand-in: 250 J per measured run."""
+    reason = None
+
+    def __init__(self, device=0):
+        self.j = None
+
+    def start(self):
+        self.j = None
+
+    def stop(self):
+        self.j = 250.0
+        return self.j
+
+    def close(self):
+        pass
+
+
 class _FakeCtx:
     def __init__(self, N, nel, L, periodic):
         self.nL = 8
@@ -118,11 +136,16 @@ class _FakeCtx:
         xyz.zero_()
 
 
-def _fake_tgv_class(histories):
-    """TGV stand-in whose KE / enstrophy follow histories[config](t)."""
+def _fake_tgv_class(histories, speed=None):
+    """TGV stand-in whose KE / enstrophy follow histories[config](t); with
+    set_dt(cfl_target=...) its steps follow the CFL rule for a CFL number of
+    speed[config] * dt."""
     class FakeTGV:
         def __init__(self, ctx, nu, dt, op, vel, pres):
-            self.dt, self.n, self.cfg = dt, 0, None
+            self.dt, self.n, self.cfg, self.t, self.target, self.dt_max = dt, 0, None, 0.0, 0.0, 0.0
+
+        def set_dt(self, dt=0.0, cfl_target=0.0, dt_max=0.0):
+            self.target, self.dt_max = cfl_target, dt_max
 
         def set_policy(self, rules):
             self.cfg = [k for k, v in policy.TABLE2.items() if all(rules[0][b] == v[b] for b in v)][0]
@@ -140,9 +163,20 @@ def _fake_tgv_class(histories):
             out = []
             for _ in range(n):
                 self.n += 1
-                t = self.n * self.dt
+                if self.target:
+                    self.t += self.dt
+                else:
+                    self.t = self.n * self.dt
+                t = self.t
+                cfl = (speed or {}).get(self.cfg, 10.0) * self.dt
                 ke, en, status = histories[self.cfg](t)
-                out.append(dict(t=t, ke=ke, enstrophy=en, iters=[3, 2, 2, 2], status=status))
+                out.append(dict(t=t, ke=ke, enstrophy=en, iters=[3, 2, 2, 2], status=status,
+                                dt=self.dt, cfl=cfl))
+                if self.target:
+                    f = min(1.1, max(0.5, self.target / cfl))
+                    self.dt = self.dt * f
+                    if self.dt_max:
+                        self.dt = min(self.dt, self.dt_max)
             return out
 
         def close(self):
@@ -236,3 +270,57 @@ def test_replay_bookkeeping_without_a_gpu(monkeypatch):
     assert r["A-4"]["e_Omega_max"] == pytest.approx(3e-7, rel=1e-3)
     assert r["B-7"]["steps"] == 3 and r["B-7"]["status"] == -5 and math.isnan(r["B-7"]["ms_per_step"])
     assert r["B-7"]["e_E_max"] == 0.0
+
+
+def _patch_gpu(monkeypatch, histories, speed=None):
+    import torch
+
+    from paper_2608_24348_gb300 import energy
+    monkeypatch.setattr(sem, "Ctx", _FakeCtx)
+    monkeypatch.setattr(sem, "TGV", _fake_tgv_class(histories, speed))
+    monkeypatch.setattr(sem, "opts", lambda **kw: kw)
+    monkeypatch.setattr(energy, "EnergyMeter", _FakeMeter)
+    monkeypatch.setattr(torch.cuda, "Event", _FakeEvent)
+    monkeypatch.setattr(torch.cuda, "Stream", _FakeStream)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: __import__("contextlib").nullcontext())
+    real_empty = torch.empty
+    monkeypatch.setattr(torch, "empty", lambda *a, device=None, **kw: real_empty(*a, **kw))
+
+
+def test_cfl_controlled_long_run_without_a_gpu(monkeypatch):
+    """CFL-controlled long run on the stand-in: the run ends at the first step
+    reaching t_end, the step settles where speed * dt = 0.4 (growth capped at
+    10 %), energy-to-solution comes from the meter, and the errors compare the
+    histories at A-0's times although the two runs step differently."""
+    import math
+
+    def a0(t):
+        return 0.125 * math.exp(-0.1 * t), 1.0 + math.exp(-(t - 3) ** 2), 0
+
+    def a1(t):
+        ke, en, _ = a0(t)
+        return ke * (1 + 1e-6), en, 0
+
+    _patch_gpu(monkeypatch, {"A-0": a0, "A-1": a1}, speed={"A-0": 40.0, "A-1": 41.0})
+    rows = policy.long_run(["A-0", "A-1"], nel=2, N=3, re=2.0, dt=1e-3, t_end=6.0, projection=0,
+                           chunk=50, every=10, cfl=0.4)
+    r = {row["config"]: row for row in rows}
+    a, b = r["A-0"], r["A-1"]
+    assert 6.0 <= a["t_reached"] < 6.0 + 0.011 and a["stopped"] is None
+    assert a["cfl_max"] == pytest.approx(0.4, rel=1e-12) and a["cfl_target"] == 0.4
+    assert 0.009 < a["dt_mean"] < 0.01                 # 0.4 / 40, after the ramp from 1e-3
+    assert a["energy_j"] == 250.0 and a["time_to_solution_s"] >= 0
+    assert a["t_peak"] == pytest.approx(3.0, abs=2e-3)
+    # A-1 steps at 0.4 / 41: its KE history, interpolated to A-0's times, is 1e-6
+    # off (plus the linear interpolation's h^2/8 |KE''| / KE, about 1.3e-7)
+    assert b["steps"] > a["steps"]
+    assert abs(b["e_E_max"] - 1e-6) < 2e-7
+    assert b["e_Omega_max"] < 1e-3
+
+
+def test_peak_on_uneven_samples():
+    """The vertex of the parabola through three unevenly spaced samples is exact
+    for a parabola."""
+    t = [0.0, 0.3, 0.5, 1.1, 1.2]
+    tp, yp = policy.peak(t, [2 - 3 * (x - 0.61) ** 2 for x in t])
+    assert tp == pytest.approx(0.61, abs=1e-12) and yp == pytest.approx(2.0, abs=1e-12)
