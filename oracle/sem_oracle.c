@@ -955,8 +955,9 @@ void orc_tgv_destroy(void *h)
 
 /* Storage precision of the stepper's state (Sec. 4: the global precision rp
  * is the storage format).  store32 != 0: the convective term, the pressure and
- * the new velocity are rounded to FP32 values where each step stores them
- * (the arithmetic stays FP64). */
+ * the new velocity are rounded to FP32 values where each step stores them,
+ * and so is the state given to orc_tgv_set after this call (with rp = fp32
+ * the whole state is FP32 from the start); the arithmetic stays FP64. */
 int orc_tgv_set_storage(void *hnd, int store32)
 {
     orc_tgv *s = hnd;
@@ -980,10 +981,15 @@ int orc_tgv_set(void *hnd, int h, const double *u0, const double *u1, const doub
     memcpy(s->u[h][0], u0, sizeof(double) * s->nL);
     memcpy(s->u[h][1], u1, sizeof(double) * s->nL);
     memcpy(s->u[h][2], u2, sizeof(double) * s->nL);
+    if (s->store32)
+        for (int c = 0; c < 3; ++c) round_to_float(s->u[h][c], s->nL);
     orc_convect(s->N, s->nelx, s->nely, s->nelz, s->vert, s->jinv, s->u[h][0], s->u[h][1],
                 s->u[h][2], s->C[h][0], s->C[h][1], s->C[h][2]);
+    if (s->store32)
+        for (int c = 0; c < 3; ++c) round_to_float(s->C[h][c], s->nL);
     if (h == 0) {
         if (p) memcpy(s->p, p, sizeof(double) * s->nL);
+        if (p && s->store32) round_to_float(s->p, s->nL);
         s->step = step;
         s->t = t;
         s->hist_dt[0] = s->hist_dt[1] = s->dt;  /* earlier levels: steps of the current size */
