@@ -346,9 +346,12 @@ SEM_API int sem_tgv_init(sem_ctx *ctx, double nu, double dt, sem_dtype op, const
  *    tolerance) or the kernel-level ax_helm overrides SEM_F16_TC / SEM_BF16_TC
  *    (16-bit tensor-core operator in that inner PCG);
  *  - storage: the global cap rp on stored state: SEM_F64, or SEM_F32 = the
- *    velocity and convection histories and the pressure are rounded to FP32
- *    values where they are stored each step (FP32 storage numerics; the buffers
- *    stay FP64).
+ *    velocity and convection histories are held in FP32 buffers (18 FP32
+ *    E-vectors, allocated by the first sem_tgv_set_policy whose rules ask for
+ *    them; read and widened by the kernels that use them), and the pressure,
+ *    which is the pressure solve's FP64 iterate, is rounded to FP32 values
+ *    where it is stored.  A change of storage between two steps moves the
+ *    histories to the other buffers (rounding to nearest towards FP32).
  * Accumulation (dot products, norms, refinement residuals, BDF/EXT sums, the
  * KE / enstrophy diagnostics) is FP64 under every rule.  first_step: the rule
  * applies from that step on (1-based; <= 1 = from the first step). */
@@ -364,7 +367,8 @@ typedef struct {
  * <= that step is in force; before the first rule starts (and with n = 0) the
  * precisions given to sem_tgv_init apply.  A change of rule between two steps
  * re-captures the step graph.  Returns SEM_ERR_ARG for an unsupported
- * precision or an unsorted schedule (the previous schedule then stays). */
+ * precision or an unsorted schedule, SEM_ERR_NOMEM if the FP32 history
+ * buffers do not fit (the previous schedule then stays). */
 SEM_API int sem_tgv_set_policy(sem_tgv *tgv, int n, const sem_tgv_policy *rules);
 
 /* Projection of the pressure solve onto previous solutions (Sec. 3: the

@@ -83,6 +83,10 @@ struct sem_tgv {
     double cfl_target, dt_max; // adaptive step when cfl_target > 0
     TgvDev *hdev;             // pinned host copy of the counters
     double *u[3][3], *C[3][3], *p, *unew[3], *F[3], *g[3], *bp, *rhs[3];
+    // FP32 storage (rp = fp32): the velocity and convection histories live in
+    // these FP32 buffers instead of u and C while storage == SEM_F32
+    float *u32[3][3], *C32[3][3];
+    float *block32;    // one allocation for them (made by the first rule that needs it)
     double *part;      // [E][2]
     double *tab64;     // eta[M], wq[M], J[M*n]
     float *tab32;
@@ -166,6 +170,20 @@ static void interp_table(int n, const double *xi, int M, const double *eta, doub
 // Dealiased convective term
 // ---------------------------------------------------------------------------
 
+// Stored fields (velocity and convection histories) are FP64, or FP32 under
+// FP32 storage; s32 selects the type at run time (warp-uniform), values are
+// widened to FP64 on load and rounded to nearest on store.
+__device__ __forceinline__ double ld_fs(const void *p, int64_t q, int s32)
+{
+    return s32 ? (double)((const float *)p)[q] : ((const double *)p)[q];
+}
+
+__device__ __forceinline__ void st_fs(void *p, int64_t q, double v, int s32)
+{
+    if (s32) ((float *)p)[q] = __double2float_rn(v);
+    else ((double *)p)[q] = v;
+}
+
 template <int NP>
 struct ConvCfg {
     static constexpr int M = (3 * NP + 1) / 2;
@@ -179,8 +197,9 @@ struct ConvCfg {
 };
 
 struct ConvArgs {
-    const double *u[3];
-    double *C[3];
+    const void *u[3];  // stored fields (FP32 when s32)
+    void *C[3];
+    int s32;
     const void *jinv;  // [E][9][n3], FP64 or FP32 per T
     const double *vert;
     const void *D;     // n*n (T)
@@ -298,7 +317,7 @@ __global__ void __launch_bounds__(256) k_convect(ConvArgs a)
         __syncthreads();
         const int64_t off = e * N3;
         for (int t = threadIdx.x; t < 3 * N3; t += blockDim.x)
-            su[t] = rnd16<R16>((T)a.u[t / N3][off + t % N3]);
+            su[t] = rnd16<R16>((T)ld_fs(a.u[t / N3], off + t % N3, a.s32));
         if (threadIdx.x < 24) {  // x = c0 + c1 r + c2 s + c3 t + c4 rs + c5 rt + c6 st + c7 rst
             const int m = threadIdx.x / 3, d = threadIdx.x % 3;
             const int ex = (int)(e % a.nelx), ey = (int)((e / a.nelx) % a.nely),
@@ -369,8 +388,8 @@ __global__ void __launch_bounds__(256) k_convect(ConvArgs a)
                 for (int q = threadIdx.x; q < M3; q += blockDim.x) sf[q] = rnd16<R16>(sf[q]);
                 __syncthreads();
             }
-            double *Cc = a.C[c] + off;
-            interp_bwd<NP, T, R16>(sf, st1, st2, sJ, [&](int pn, T v) { Cc[pn] = (double)v; });
+            void *Cc = a.C[c];
+            interp_bwd<NP, T, R16>(sf, st1, st2, sJ, [&](int pn, T v) { st_fs(Cc, off + pn, (double)v, a.s32); });
         }
     }
 }
@@ -383,24 +402,30 @@ struct Coef {
     double a[3], b[3], b0, dt;
 };
 
-__global__ void k_tgv_F(const double *C00, const double *C01, const double *C02, const double *C10,
-                        const double *C11, const double *C12, const double *C20, const double *C21,
-                        const double *C22, double *F0, double *F1, double *F2, Coef k, int64_t nL)
+struct FArgs {
+    const void *C[3][3];  // [level][comp], stored fields
+    double *F[3];
+    int s32;
+};
+
+__global__ void k_tgv_F(FArgs a, Coef k, int64_t nL)
 {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= nL) return;
-    F0[q] = -(k.a[0] * C00[q] + k.a[1] * C10[q] + k.a[2] * C20[q]);
-    F1[q] = -(k.a[0] * C01[q] + k.a[1] * C11[q] + k.a[2] * C21[q]);
-    F2[q] = -(k.a[0] * C02[q] + k.a[1] * C12[q] + k.a[2] * C22[q]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        a.F[c][q] = -(k.a[0] * ld_fs(a.C[0][c], q, a.s32) + k.a[1] * ld_fs(a.C[1][c], q, a.s32) +
+                      k.a[2] * ld_fs(a.C[2][c], q, a.s32));
 }
 
 struct GArgs {
     const double *F[3];
-    const double *u[3][3];  // [level][comp]
+    const void *u[3][3];  // [level][comp], stored fields
     double *g[3];
     const double *geo64;
     GsDesc gs;
     Coef k;
+    int s32;
 };
 
 // g_c = dssum(F_c) / dssum(B) + sum_j b_j u^{n+1-j}_c / dt at every copy.
@@ -420,7 +445,8 @@ __global__ void k_tgv_g(GArgs a)
     for (int c = 0; c < 3; ++c) {
         double s = 0.0;
         for (int t = 0; t < m; ++t) s += a.F[c][idx[t]];
-        const double hist = a.k.b[0] * a.u[0][c][f] + a.k.b[1] * a.u[1][c][f] + a.k.b[2] * a.u[2][c][f];
+        const double hist = a.k.b[0] * ld_fs(a.u[0][c], f, a.s32) + a.k.b[1] * ld_fs(a.u[1][c], f, a.s32) +
+                            a.k.b[2] * ld_fs(a.u[2][c], f, a.s32);
         const double v = s / bs + hist / a.k.dt;
         for (int t = 0; t < m; ++t) a.g[c][idx[t]] = v;
     }
@@ -466,7 +492,8 @@ __global__ void k_tgv_divg(const double *g0, const double *g1, const double *g2,
 
 struct VArgs {
     const double *F[3];
-    const double *u[3][3];
+    const void *u[3][3];  // stored fields
+    int s32;
     const double *p;
     const double *jinv, *geo64, *D;
     double *rhs[3];
@@ -503,8 +530,8 @@ __global__ void k_tgv_vrhs(VArgs a)
             for (int c = 0; c < 3; ++c) {
                 const double dpdx = ji[(0 * 3 + c) * N3] * gr + ji[(1 * 3 + c) * N3] * gs +
                                     ji[(2 * 3 + c) * N3] * gt;
-                const double hist = a.k.b[0] * a.u[0][c][q] + a.k.b[1] * a.u[1][c][q] +
-                                    a.k.b[2] * a.u[2][c][q];
+                const double hist = a.k.b[0] * ld_fs(a.u[0][c], q, a.s32) + a.k.b[1] * ld_fs(a.u[1][c], q, a.s32) +
+                                    a.k.b[2] * ld_fs(a.u[2][c], q, a.s32);
                 a.rhs[c][q] = a.F[c][q] + bm * (hist / a.k.dt - dpdx);
             }
         }
@@ -522,7 +549,7 @@ struct GapInv {
 };
 
 template <int NP, typename T>
-__global__ void k_tgv_diag_part(const double *u0, const double *u1, const double *u2,
+__global__ void k_tgv_diag_part(const void *u0, const void *u1, const void *u2, int s32,
                                 const T *jinv, const T *geo, const T *D, GapInv ig, double *part, int64_t E)
 {
     constexpr int N3 = NP * NP * NP;
@@ -530,11 +557,11 @@ __global__ void k_tgv_diag_part(const double *u0, const double *u1, const double
     __shared__ T sD[NP * NP];
     __shared__ double sred[3 * 32];
     for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sD[t] = D[t];
-    const double *uu[3] = {u0, u1, u2};
+    const void *uu[3] = {u0, u1, u2};
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         __syncthreads();
         const int64_t off = e * N3;
-        for (int t = threadIdx.x; t < 3 * N3; t += blockDim.x) su[t] = T(uu[t / N3][off + t % N3]);
+        for (int t = threadIdx.x; t < 3 * N3; t += blockDim.x) su[t] = T(ld_fs(uu[t / N3], off + t % N3, s32));
         __syncthreads();
         T tke = 0, ten = 0;
         double cmax = 0.0;
@@ -653,6 +680,19 @@ __global__ void k_tgv_log_iters(const char *state, int stride, int iters_off, in
     }
 }
 
+// Copy n values between FP64 and FP32 buffers (narrowing rounds to nearest).
+__global__ void k_conv_f64_f32(const double *__restrict__ a, float *__restrict__ b, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        b[t] = __double2float_rn(a[t]);
+}
+
+__global__ void k_conv_f32_f64(const float *__restrict__ a, double *__restrict__ b, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        b[t] = (double)a[t];
+}
+
 // FP64 values as float pairs (hi = round(v), lo = round(v - hi)).
 __global__ void k_split_df64(const double *__restrict__ a, df64 *__restrict__ out, int64_t n)
 {
@@ -680,8 +720,20 @@ static int run_convect(const ConvArgs &a, int grid, size_t smem, cudaStream_t s)
     return SEM_OK;
 }
 
+// The stored fields in force: FP32 buffers under FP32 storage, else FP64.
+static bool stored32(const sem_tgv *T) { return T->storage == SEM_F32; }
+static void *fu(const sem_tgv *T, int l, int c) { return stored32(T) ? (void *)T->u32[l][c] : (void *)T->u[l][c]; }
+static void *fC(const sem_tgv *T, int l, int c) { return stored32(T) ? (void *)T->C32[l][c] : (void *)T->C[l][c]; }
+
+static unsigned conv_grid(int64_t n)
+{
+    const int64_t b = sem_ceil_div(n, 256);
+    return (unsigned)(b < 65535 * 8 ? b : 65535 * 8);
+}
+
+// Convective term of history level `level` (stored velocity -> stored C).
 template <int NP>
-static int launch_convect(sem_tgv *T, const double *const u[3], double *const C[3], cudaStream_t s)
+static int launch_convect(sem_tgv *T, int level, cudaStream_t s)
 {
     sem_ctx *c = T->c;
     const bool f32 = T->op != SEM_F64 && T->op != SEM_F64_NATIVE;
@@ -689,9 +741,10 @@ static int launch_convect(sem_tgv *T, const double *const u[3], double *const C[
     if (smem > 227 * 1024) return SEM_ERR_ARG;
     ConvArgs a;
     for (int k = 0; k < 3; ++k) {
-        a.u[k] = u[k];
-        a.C[k] = C[k];
+        a.u[k] = fu(T, level, k);
+        a.C[k] = fC(T, level, k);
     }
+    a.s32 = stored32(T);
     a.vert = c->vert;
     a.nelx = c->nelx;
     a.nely = c->nely;
@@ -727,6 +780,8 @@ __global__ void k_round_f32(double *__restrict__ a, int64_t n)
         a[t] = (double)__double2float_rn(a[t]);
 }
 
+// The pressure (the solver's iterate) stays an FP64 buffer; under FP32
+// storage its values are rounded to FP32 values where it is stored.
 static int round_stored(sem_tgv *T, double *a, int64_t n, cudaStream_t s)
 {
     if (T->storage != SEM_F32) return SEM_OK;
@@ -750,10 +805,33 @@ static int round_stored(sem_tgv *T, double *a, int64_t n, cudaStream_t s)
         default: return SEM_ERR_ARG;        \
     }
 
-static int convect(sem_tgv *T, const double *const u[3], double *const C[3], cudaStream_t s)
+static int convect(sem_tgv *T, int level, cudaStream_t s)
 {
-    TGV_DISPATCH(T->c->n, return launch_convect<NP>(T, u, C, s));
+    TGV_DISPATCH(T->c->n, return launch_convect<NP>(T, level, s));
     return SEM_ERR_ARG;
+}
+
+// Move the histories between the FP64 and FP32 buffers (a change of storage
+// precision between two steps; narrowing rounds to nearest).
+static int move_storage(sem_tgv *T, bool to32, cudaStream_t s)
+{
+    const int64_t nL = T->c->nL;
+    for (int l = 0; l < 3; ++l)
+        for (int k = 0; k < 3; ++k) {
+            if (to32) {
+                k_conv_f64_f32<<<conv_grid(nL), 256, 0, s>>>(T->u[l][k], T->u32[l][k], nL);
+                k_conv_f64_f32<<<conv_grid(nL), 256, 0, s>>>(T->C[l][k], T->C32[l][k], nL);
+            } else {
+                k_conv_f32_f64<<<conv_grid(nL), 256, 0, s>>>(T->u32[l][k], T->u[l][k], nL);
+                k_conv_f32_f64<<<conv_grid(nL), 256, 0, s>>>(T->C32[l][k], T->C[l][k], nL);
+            }
+            SEM_CHECK_LAUNCH();
+        }
+    if (to32) {  // the pressure stays an FP64 buffer holding FP32 values
+        k_round_f32<<<conv_grid(nL), 256, 0, s>>>(T->p, nL);
+        SEM_CHECK_LAUNCH();
+    }
+    return SEM_OK;
 }
 
 // BDF_q / EXT_q coefficients for the step h0 = t^{n+1} - t^n after steps h1,
@@ -815,8 +893,8 @@ static int diag(sem_tgv *T, int advance, cudaStream_t s)
     const int blocks = (int)(c->E < 65535 * 16 ? c->E : 65535 * 16);
     // FP64-accurate on the FP32 pipes (J^-1, B and D as float pairs)
     TGV_DISPATCH(c->n, k_tgv_diag_part<NP, df64><<<blocks, 256, 0, s>>>(
-                           T->u[0][0], T->u[0][1], T->u[0][2], T->jinvdf, (const df64 *)c->geodf,
-                           (const df64 *)c->tabdf, gap_inv(c), T->part, c->E));
+                           fu(T, 0, 0), fu(T, 0, 1), fu(T, 0, 2), (int)stored32(T), T->jinvdf,
+                           (const df64 *)c->geodf, (const df64 *)c->tabdf, gap_inv(c), T->part, c->E));
     SEM_CHECK_LAUNCH();
     const double V = c->volume;
     k_tgv_diag_final<<<1, 256, 0, s>>>(T->part, c->E, V, T->dt, T->dev, T->log, advance);
@@ -835,23 +913,27 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     const size_t bytes = sizeof(double) * nL;
     const Coef k = coef(q, T->dt, T->hist_dt[0], T->hist_dt[1]);
     int rc;
+    const int s32 = stored32(T);
     // 1. convective term of the current velocity (stored: C history)
-    rc = convect(T, T->u[0], T->C[0], s);
-    if (rc) return rc;
-    rc = round_stored(T, T->C[0][0], 3 * nL, s);
+    rc = convect(T, 0, s);
     if (rc) return rc;
     // 2. extrapolated convection
-    k_tgv_F<<<(unsigned)sem_ceil_div(nL, 256), 256, 0, s>>>(
-        T->C[0][0], T->C[0][1], T->C[0][2], T->C[1][0], T->C[1][1], T->C[1][2], T->C[2][0],
-        T->C[2][1], T->C[2][2], T->F[0], T->F[1], T->F[2], k, nL);
+    FArgs fa;
+    for (int cc = 0; cc < 3; ++cc) {
+        fa.F[cc] = T->F[cc];
+        for (int l = 0; l < 3; ++l) fa.C[l][cc] = fC(T, l, cc);
+    }
+    fa.s32 = s32;
+    k_tgv_F<<<(unsigned)sem_ceil_div(nL, 256), 256, 0, s>>>(fa, k, nL);
     SEM_CHECK_LAUNCH();
     // 3. strong right-hand side g
     GArgs ga;
     for (int cc = 0; cc < 3; ++cc) {
         ga.F[cc] = T->F[cc];
         ga.g[cc] = T->g[cc];
-        for (int l = 0; l < 3; ++l) ga.u[l][cc] = T->u[l][cc];
+        for (int l = 0; l < 3; ++l) ga.u[l][cc] = fu(T, l, cc);
     }
+    ga.s32 = s32;
     ga.geo64 = c->geo64;
     ga.gs = sem_gs_desc(c);
     ga.k = k;
@@ -881,8 +963,9 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     for (int cc = 0; cc < 3; ++cc) {
         va.F[cc] = T->F[cc];
         va.rhs[cc] = T->rhs[cc];
-        for (int l = 0; l < 3; ++l) va.u[l][cc] = T->u[l][cc];
+        for (int l = 0; l < 3; ++l) va.u[l][cc] = fu(T, l, cc);
     }
+    va.s32 = s32;
     va.p = T->p;
     va.jinv = c->jinv64;
     va.geo64 = c->geo64;
@@ -894,7 +977,12 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     for (int cc = 0; cc < 3; ++cc) {
         rc = sem_dssum_dev(c, T->rhs[cc], SEM_F64, s);
         if (rc) return rc;
-        SEM_CUDA(cudaMemcpyAsync(T->unew[cc], T->u[0][cc], bytes, cudaMemcpyDeviceToDevice, s));
+        if (s32) {
+            k_conv_f32_f64<<<conv_grid(nL), 256, 0, s>>>(T->u32[0][cc], T->unew[cc], nL);
+            SEM_CHECK_LAUNCH();
+        } else {
+            SEM_CUDA(cudaMemcpyAsync(T->unew[cc], T->u[0][cc], bytes, cudaMemcpyDeviceToDevice, s));
+        }
     }
     const double *bb[3] = {T->rhs[0], T->rhs[1], T->rhs[2]};
     double *xx[3] = {T->unew[0], T->unew[1], T->unew[2]};
@@ -904,15 +992,19 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     k_tgv_log_iters<<<1, 32, 0, s>>>(st0, stride, io, so, serr, 1, 3, T->dev, T->log, 0);
     SEM_CHECK_LAUNCH();
     // 6. shift histories (copies keep every buffer address fixed for graph replay)
+    const size_t sbytes = (s32 ? sizeof(float) : sizeof(double)) * nL;
     for (int cc = 0; cc < 3; ++cc) {
-        SEM_CUDA(cudaMemcpyAsync(T->u[2][cc], T->u[1][cc], bytes, cudaMemcpyDeviceToDevice, s));
-        SEM_CUDA(cudaMemcpyAsync(T->u[1][cc], T->u[0][cc], bytes, cudaMemcpyDeviceToDevice, s));
-        SEM_CUDA(cudaMemcpyAsync(T->u[0][cc], T->unew[cc], bytes, cudaMemcpyDeviceToDevice, s));
-        SEM_CUDA(cudaMemcpyAsync(T->C[2][cc], T->C[1][cc], bytes, cudaMemcpyDeviceToDevice, s));
-        SEM_CUDA(cudaMemcpyAsync(T->C[1][cc], T->C[0][cc], bytes, cudaMemcpyDeviceToDevice, s));
+        SEM_CUDA(cudaMemcpyAsync(fu(T, 2, cc), fu(T, 1, cc), sbytes, cudaMemcpyDeviceToDevice, s));
+        SEM_CUDA(cudaMemcpyAsync(fu(T, 1, cc), fu(T, 0, cc), sbytes, cudaMemcpyDeviceToDevice, s));
+        if (s32) {  // the new velocity, rounded to FP32 where it is stored
+            k_conv_f64_f32<<<conv_grid(nL), 256, 0, s>>>(T->unew[cc], T->u32[0][cc], nL);
+            SEM_CHECK_LAUNCH();
+        } else {
+            SEM_CUDA(cudaMemcpyAsync(T->u[0][cc], T->unew[cc], bytes, cudaMemcpyDeviceToDevice, s));
+        }
+        SEM_CUDA(cudaMemcpyAsync(fC(T, 2, cc), fC(T, 1, cc), sbytes, cudaMemcpyDeviceToDevice, s));
+        SEM_CUDA(cudaMemcpyAsync(fC(T, 1, cc), fC(T, 0, cc), sbytes, cudaMemcpyDeviceToDevice, s));
     }
-    rc = round_stored(T, T->u[0][0], 3 * nL, s);  // the new velocity
-    if (rc) return rc;
     return diag(T, 1, s);
 }
 
@@ -923,6 +1015,7 @@ extern "C" void sem_tgv_destroy(sem_tgv *T)
     if (T->graph_state == 1) cudaGraphExecDestroy(T->graph);
     proj_free(T);
     if (T->block) cudaFree(T->block);
+    if (T->block32) cudaFree(T->block32);
     if (T->part) cudaFree(T->part);
     if (T->tab64) cudaFree(T->tab64);
     if (T->tab32) cudaFree(T->tab32);
@@ -1055,13 +1148,17 @@ extern "C" int sem_tgv_set(sem_tgv *T, int level, const double *u, const double 
     for (int k = 0; k < 3; ++k) {
         int rc = stage_field(T->c, src[k], T->u[level][k], s);
         if (rc) return rc;
+        if (stored32(T)) {
+            k_conv_f64_f32<<<conv_grid(T->c->nL), 256, 0, s>>>(T->u[level][k], T->u32[level][k], T->c->nL);
+            SEM_CHECK_LAUNCH();
+        }
     }
     if (level == 0 && p) {
         int rc = stage_field(T->c, p, T->p, s);
         if (rc) return rc;
     }
     if (level > 0) {  // history of the convective term at that level
-        int rc = convect(T, T->u[level], T->C[level], s);
+        int rc = convect(T, level, s);
         if (rc) return rc;
     }
     if (level == 0) {
@@ -1341,6 +1438,22 @@ extern "C" int sem_tgv_set_policy(sem_tgv *T, int n, const sem_tgv_policy *rules
             return SEM_ERR_ARG;
         if (r > 0 && p.first_step < rules[r - 1].first_step) return SEM_ERR_ARG;
     }
+    bool need32 = false;
+    for (int r = 0; r < n; ++r) need32 |= rules[r].storage == SEM_F32;
+    if (need32 && !T->block32) {  // FP32 history buffers: 18 FP32 E-vectors
+        const int64_t nL = T->c->nL;
+        cudaError_t e = cudaMalloc(&T->block32, sizeof(float) * 18 * nL);
+        if (e != cudaSuccess) {
+            sem_note_cuda_error(e, "cudaMalloc(FP32 histories)");
+            T->block32 = nullptr;
+            return e == cudaErrorMemoryAllocation ? SEM_ERR_NOMEM : SEM_ERR_CUDA;
+        }
+        float *b = T->block32;
+        for (int l = 0; l < 3; ++l)
+            for (int k = 0; k < 3; ++k) { T->u32[l][k] = b; b += nL; }
+        for (int l = 0; l < 3; ++l)
+            for (int k = 0; k < 3; ++k) { T->C32[l][k] = b; b += nL; }
+    }
     for (int r = 0; r < n; ++r) T->rules[r] = rules[r];
     T->nrules = n;
     T->cur_rule = -2;  // re-applied before the next step
@@ -1348,13 +1461,15 @@ extern "C" int sem_tgv_set_policy(sem_tgv *T, int n, const sem_tgv_policy *rules
 }
 
 // Put the rule in force at step `step` (1-based) into effect; a change drops
-// the captured step graph so that the next steady step is captured again.
-static void apply_policy(sem_tgv *T, int step)
+// the captured step graph so that the next steady step is captured again, and
+// a change of storage precision moves the histories to the other buffers.
+static int apply_policy(sem_tgv *T, int step, cudaStream_t s)
 {
     int r = -1;
     for (int k = 0; k < T->nrules; ++k)
         if (T->rules[k].first_step <= step) r = k;
-    if (r == T->cur_rule) return;
+    if (r == T->cur_rule) return SEM_OK;
+    const bool was32 = stored32(T);
     if (r < 0) {
         T->op = T->op0;
         T->vo.inner = T->vin0;
@@ -1372,6 +1487,8 @@ static void apply_policy(sem_tgv *T, int step)
     }
     T->graph_warm = 0;
     T->cur_rule = r;
+    if (was32 != stored32(T)) return move_storage(T, stored32(T), s);
+    return SEM_OK;
 }
 
 // Advance nsteps steps on stream s (no synchronisation).
@@ -1382,8 +1499,8 @@ static int advance(sem_tgv *T, int nsteps, cudaStream_t s)
         const bool adaptive = T->cfl_target > 0;
         // graph replay only for third-order steps of one fixed size
         const bool steady = q == 3 && !adaptive && T->hist_dt[0] == T->dt && T->hist_dt[1] == T->dt;
-        int rc;
-        apply_policy(T, T->step + 1);
+        int rc = apply_policy(T, T->step + 1, s);
+        if (rc) return rc;
         if (steady && s != 0 && T->graph_state == 0 && !T->graph_warm) {
             // one steady step runs directly first, so the Jacobi inverses of its
             // solves are cached when the next one is captured (the graph then
@@ -1491,6 +1608,11 @@ extern "C" int sem_tgv_get(sem_tgv *T, double *u, double *v, double *w, double *
     const double *src[4] = {T->u[0][0], T->u[0][1], T->u[0][2], T->p};
     for (int k = 0; k < 4; ++k) {
         if (!dst[k]) continue;
+        if (k < 3 && stored32(T)) {  // widened through the (between steps unused) new-velocity buffer
+            k_conv_f32_f64<<<conv_grid(T->c->nL), 256, 0, s>>>(T->u32[0][k], T->unew[k], T->c->nL);
+            SEM_CHECK_LAUNCH();
+            src[k] = T->unew[k];
+        }
         const cudaMemcpyKind kind = sem_is_device_ptr(dst[k]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         SEM_CUDA(cudaMemcpyAsync(dst[k], src[k], bytes, kind, s));
     }
