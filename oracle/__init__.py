@@ -5,8 +5,10 @@ Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 (``paper_2608_24348_gb300``); the two meet only through the seeded input
 generators in ``paper_2608_24348_gb300.inputs``.
 
-Everything is computed by ``sem_oracle.c`` (plain C, FP64, OpenMP), compiled
-on first use into ``oracle/_build/liboracle.so``.  The SEM definitions follow
+Everything is computed by ``sem_oracle.c`` and ``sem_oracle_hsmg.c`` (the
+pressure solver: GMRES with the hybrid Schwarz multigrid preconditioner) --
+plain C, FP64, OpenMP -- compiled on first use into
+``oracle/_build/liboracle.so``.  The SEM definitions follow
 the textbook spectral-element method (Deville, Fischer & Mund 2002), which is
 what the paper's Neko solver implements (Sec. 2, Sec. 3); the paper prints no
 SEM formula itself.  Each function's docstring names the component of the
@@ -31,7 +33,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "sem_oracle.c")
+_SRCS = [os.path.join(_HERE, "sem_oracle.c"), os.path.join(_HERE, "sem_oracle_hsmg.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -47,11 +49,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle shared library (gcc, -O2, OpenMP, no FP contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=gnu11", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
-           "-o", tmp, _SRC, "-lm"]
+           "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -93,6 +95,26 @@ def lib():
             L.orc_tgv_get.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
             L.orc_tgv_step.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
             L.orc_tgv_set_storage.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_fdm_1d.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     _dp, _dp, _dp, _dp]
+            L.orc_fdm_apply.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_double,
+                                        ctypes.c_double, _dp, _dp]
+            L.orc_hsmg_create.restype = ctypes.c_void_p
+            L.orc_hsmg_create.argtypes = [ctypes.c_int, _ip, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          _ip, _dp, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int]
+            L.orc_hsmg_destroy.argtypes = [ctypes.c_void_p]
+            for f in ("orc_hsmg_prolong", "orc_hsmg_restrict", "orc_hsmg_smooth"):
+                getattr(L, f).argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp]
+            L.orc_hsmg_apply.argtypes = [ctypes.c_void_p, _dp, _dp]
+            L.orc_hsmg_coarse_stats.argtypes = [ctypes.c_void_p, _dp, _dp]
+            L.orc_hsmg_coarse_stats.restype = None
+            L.orc_fgmres.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4 + [_ip, _dp, _dp, _dp,
+                                                                              ctypes.c_double,
+                                                                              ctypes.c_double, _dp, _dp,
+                                                                              ctypes.c_double,
+                                                                              ctypes.c_int, ctypes.c_int,
+                                                                              ctypes.c_int, _dp, _dp]
             _lib = L
     return _lib
 
@@ -338,3 +360,105 @@ class TGV:
             lib().orc_tgv_destroy(self._h)
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------
+# Pressure solver: flexible GMRES with the hybrid Schwarz multigrid (Sec. 1, Sec. 3)
+# ----------------------------------------------------------------------------
+
+def fdm_1d(N, h, hl=0.0, hr=0.0):
+    """1-D factors of the fast-diagonalisation local solve: (S, lam, K, Mdiag) with
+    K S = M S diag(lam), S^T M S = I (K, M: the element's 1-D stiffness and mass,
+    extended to the neighbours' first interior GLL nodes; hl, hr = 0: no neighbour)."""
+    n = N + 1
+    S, lam, K, M = np.zeros((n, n)), np.zeros(n), np.zeros((n, n)), np.zeros(n)
+    rc = lib().orc_fdm_1d(int(N), float(h), float(hl), float(hr), _p(S), _p(lam), _p(K), _p(M))
+    if rc != OK:
+        raise ValueError(f"orc_fdm_1d: {rc}")
+    return S, lam, K, M
+
+
+def fdm_apply(N, factors, h1, h2, r):
+    """A~^{-1} r on one element from three directions' (S, lam) factors."""
+    (Sx, lx), (Sy, ly), (Sz, lz) = [(_f64(S), _f64(lam)) for S, lam in factors]
+    z = np.zeros((N + 1) ** 3)
+    lib().orc_fdm_apply(int(N), _p(Sx), _p(lx), _p(Sy), _p(ly), _p(Sz), _p(lz), float(h1),
+                        float(h2), _p(_f64(r).reshape(-1)), _p(z))
+    return z
+
+
+class HSMG:
+    """Hybrid Schwarz multigrid hierarchy of orders `orders` (finest first) on a mesh."""
+
+    def __init__(self, orders, nel, vert, periodic=(1, 1, 1), h1=1.0, h2=0.0, ctol=1e-2,
+                 cmaxit=1000):
+        self.orders = [int(o) for o in orders]
+        self.nel = tuple(int(v) for v in nel)
+        self.E = self.nel[0] * self.nel[1] * self.nel[2]
+        self._o, op = _ipt(self.orders)
+        self._pd, pp = _ipt([int(bool(p)) for p in periodic])
+        self._vert = _f64(vert).reshape(-1)
+        h = lib().orc_hsmg_create(len(self.orders), op, *self.nel, pp, _p(self._vert), float(h1),
+                                  float(h2), float(ctol), int(cmaxit))
+        if not h:
+            raise ValueError("orc_hsmg_create rejected the hierarchy")
+        self._h = ctypes.c_void_p(h)
+
+    def nL(self, level=0):
+        return self.E * (self.orders[level] + 1) ** 3
+
+    def apply(self, r):
+        z = np.zeros(self.nL())
+        lib().orc_hsmg_apply(self._h, _p(_f64(r).reshape(-1)), _p(z))
+        return z
+
+    def smooth(self, level, r):
+        z = np.zeros(self.nL(level))
+        lib().orc_hsmg_smooth(self._h, int(level), _p(_f64(r).reshape(-1)), _p(z))
+        return z
+
+    def prolong(self, level, u):
+        out = np.zeros(self.nL(level))
+        lib().orc_hsmg_prolong(self._h, int(level), _p(_f64(u).reshape(-1)), _p(out))
+        return out
+
+    def restrict(self, level, r):
+        out = np.zeros(self.nL(level + 1))
+        lib().orc_hsmg_restrict(self._h, int(level), _p(_f64(r).reshape(-1)), _p(out))
+        return out
+
+    def coarse_stats(self):
+        a, b = np.zeros(1), np.zeros(1)
+        lib().orc_hsmg_coarse_stats(self._h, _p(a), _p(b))
+        return int(a[0]), int(b[0])
+
+    def __del__(self):
+        try:
+            lib().orc_hsmg_destroy(self._h)
+        except Exception:
+            pass
+
+
+def fgmres(b, x0=None, hsmg=None, mesh=None, h1=1.0, h2=0.0, tol=1e-10, abs_tol=False, m=30,
+           maxit=1000, history=False):
+    """Flexible GMRES(m) on the finest level of `hsmg` (preconditioned by it) or on
+    `mesh` (an oracle Mesh, no preconditioner).  Returns (x, status, info) with info
+    = {iters, rnorm, bnorm, restarts} (and "hist", the Arnoldi residual estimates)."""
+    b = _f64(b).reshape(-1)
+    x = np.zeros_like(b) if x0 is None else _f64(x0).reshape(-1).copy()
+    out = np.zeros(4)
+    hist = np.zeros(maxit + 1) if history else None
+    if hsmg is not None:
+        pd, pp = _ipt([1, 1, 1])
+        st = lib().orc_fgmres(hsmg._h, 0, 0, 0, 0, pp, None, None, None, 0.0, 0.0, _p(b), _p(x),
+                              float(tol), int(bool(abs_tol)), int(m), int(maxit), _p(out),
+                              _p(hist) if history else None)
+    else:
+        pd, pp = _ipt(mesh.periodic)
+        st = lib().orc_fgmres(None, mesh.N, *mesh.nel, pp, _p(mesh.D), _p(mesh.G), _p(mesh.B),
+                              float(h1), float(h2), _p(b), _p(x), float(tol), int(bool(abs_tol)),
+                              int(m), int(maxit), _p(out), _p(hist) if history else None)
+    info = dict(iters=int(out[0]), rnorm=float(out[1]), bnorm=float(out[2]), restarts=int(out[3]))
+    if history:
+        info["hist"] = hist[:info["iters"] + 1]
+    return x, st, info
