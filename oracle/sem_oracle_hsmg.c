@@ -463,9 +463,9 @@ int orc_hsmg_smooth(void *hnd, int l, const double *r, double *z)
 
 /* Solve dssum(h1 A + h2 B) x = b on the finest level of H (or, with hnd ==
  * NULL, on the order-N mesh given by N, D, G, B with no preconditioner).
- * Stopping test on the true assembled residual ||b - A x|| <= tol (abs_tol)
- * or tol ||b||, checked by the Arnoldi estimate inside a cycle and by the true
- * residual at every restart.  With h2 == 0 b loses its mean first and x its
+ * Stopping test ||b - A x|| <= tol (abs_tol) or tol ||b||, met by the true
+ * assembled residual at a restart or by the Arnoldi estimate inside a cycle
+ * (the usual GMRES test; out[1] reports the true residual).  With h2 == 0 b loses its mean first and x its
  * B-weighted mean at the end, as in orc_pcg.  out[0] = iterations, out[1] =
  * final true ||r||, out[2] = ||b||, out[3] = restarts; hist (may be NULL,
  * maxit + 1 entries) receives the Arnoldi residual estimate after each
@@ -508,7 +508,7 @@ int orc_fgmres(void *hnd, int N, int nelx, int nely, int nelz, const int *period
     for (size_t q = 0; q < nL; ++q) r[q] = b[q] - w[q];
     double beta = sqrt(orc_glsc3(E, n3, r, r, imult));
     if (hist) hist[0] = beta;
-    int it = 0, restarts = 0, status = ORC_ERR_NOT_CONVERGED;
+    int it = 0, restarts = 0, status = ORC_ERR_NOT_CONVERGED, met = 0;
     if (!isfinite(beta)) status = ORC_ERR_BREAKDOWN;
     else if (beta <= target) status = ORC_OK;
     while (status == ORC_ERR_NOT_CONVERGED && it < maxit) {
@@ -542,7 +542,7 @@ int orc_fgmres(void *hnd, int N, int nelx, int nely, int nelz, const int *period
             ++it;
             k = j + 1;
             if (hist) hist[it] = fabs(g[j + 1]);
-            if (fabs(g[j + 1]) <= target || hn == 0.0) break;
+            if (fabs(g[j + 1]) <= target || hn == 0.0) { met = 1; break; }
             for (size_t q = 0; q < nL; ++q) V[nL * (j + 1) + q] = w[q] / hn;
         }
         /* y = R^{-1} g, x += Z y */
@@ -559,7 +559,7 @@ int orc_fgmres(void *hnd, int N, int nelx, int nely, int nelz, const int *period
         beta = sqrt(orc_glsc3(E, n3, r, r, imult));
         if (status == ORC_ERR_BREAKDOWN) break;
         if (!isfinite(beta)) { status = ORC_ERR_BREAKDOWN; break; }
-        if (beta <= target) { status = ORC_OK; break; }
+        if (beta <= target || met) { status = ORC_OK; break; }
         ++restarts;
     }
 #undef AOP
