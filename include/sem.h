@@ -303,6 +303,59 @@ SEM_API int sem_tune_inner(sem_ctx *ctx, int iters, double *ms, int *best);
  * result): 0 FP32 CUDA cores, 1 split FP16 tensor cores (N <= 7). */
 SEM_API int sem_set_inner_path(int N, int path);
 
+/* ---- Pressure solver: flexible GMRES + hybrid Schwarz multigrid (Sec. 1, Sec. 3) ---- */
+
+typedef struct sem_hsmg sem_hsmg;
+
+/* Hybrid Schwarz multigrid preconditioner of h1 A + h2 B on ctx's mesh (the
+ * paper's pressure solver uses GMRES with a three-level HSMG whose coarse
+ * problem is solved by CG + Jacobi).  nlev = 1..3 levels of polynomial orders
+ * orders[0] = ctx's N > orders[1] > ... (e.g. {N, 3, 1}); N <= 9.  One
+ * application is a V-cycle: on every level but the last, an overlapping
+ * Schwarz smoother (element solves of the separable box operator extended to
+ * the neighbours' first interior GLL nodes, by fast diagonalisation, averaged
+ * over shared nodes), the level residual, restriction (transpose of Lagrange
+ * interpolation); on the last level Jacobi-PCG in FP64 to relative tolerance
+ * coarse_tol within coarse_maxit iterations; then prolongation and
+ * correction.  dtype: SEM_F32 or SEM_F64, the precision of the V-cycle
+ * (smoother, transfers, level operators).  Creates one context per coarser
+ * level (sem_setup on the same vertices) and allocates about 3 E-vectors per
+ * level plus the factor tables; the caller's ctx must outlive the object.
+ * SEM_ERR_ARG: bad orders, N > 9, dtype, h1 <= 0, h2 < 0, coarse_tol <= 0 or
+ * coarse_maxit < 1; SEM_ERR_NOMEM. */
+SEM_API int sem_hsmg_create(sem_ctx *ctx, int nlev, const int *orders, double h1, double h2,
+                            sem_dtype dtype, double coarse_tol, int coarse_maxit, sem_hsmg **out);
+
+/* z = M^{-1} r: one V-cycle (r, z: FP64 E-vectors in device memory, continuous
+ * across shared nodes as an assembled residual is; z is continuous).
+ * Stream-ordered.  SEM_ERR_ARG: NULL or host pointers. */
+SEM_API int sem_hsmg_apply(sem_hsmg *hsmg, const double *r, double *z, void *stream);
+
+/* Flexible GMRES(restart) on dssum(h1 A + h2 B) x = b with the operator and
+ * coefficients of hsmg's finest level, right-preconditioned by one V-cycle per
+ * iteration (precond != 0) or not at all.  b, x: FP64 E-vectors in device
+ * memory; x holds the initial guess and receives the solution.  opts: tol,
+ * abs_tol and maxit as for sem_pcg_solve (inner, inner_tol, max_outer,
+ * wait_timeout_s unused).  The operator is sem_ax's FP64-accurate one (the
+ * native FP64 operator for a relative tol below 1e-11); inner products are
+ * FP64 over unique nodes; with h2 == 0 b loses its mean and x its B-weighted
+ * mean.  restart: 1..64 Krylov vectors per cycle (storage: 2 restart + 3
+ * FP64 E-vectors, allocated on first use and kept).  Synchronises the stream
+ * (the host solves the Hessenberg least-squares problem and reads three
+ * inner-product sets per iteration).  Converged (SEM_OK) when the true
+ * residual, or the Arnoldi estimate of a cycle, meets the target; the true
+ * residual then may exceed it by the operator's rounding floor (the
+ * FP64-accurate operator's relative error, a few 1e-13, times ||A|| ||x||).
+ * info: iters (GMRES iterations), outer_iters (restarts), final_rnorm (true
+ * residual), bnorm.  Returns info->status (SEM_OK, SEM_ERR_NOT_CONVERGED,
+ * SEM_ERR_BREAKDOWN) or an error. */
+SEM_API int sem_gmres_solve(sem_hsmg *hsmg, int precond, const double *b, double *x,
+                            const sem_solve_opts *opts, int restart, sem_solve_info *info,
+                            void *stream);
+
+/* Free (NULL allowed; synchronises the device; destroys the coarser contexts). */
+SEM_API void sem_hsmg_destroy(sem_hsmg *hsmg);
+
 /* ---- Taylor-Green vortex stepper (Sec. 3) ---- */
 
 typedef struct {
@@ -396,6 +449,22 @@ SEM_API int sem_tgv_set_projection(sem_tgv *tgv, int max_vectors);
  * graph once three steps of the new size have run.  SEM_ERR_ARG: NULL tgv or
  * a negative or NaN argument. */
 SEM_API int sem_tgv_set_dt(sem_tgv *tgv, double dt, double cfl_target, double dt_max);
+
+/* Pressure solver of the stepper: kind 0 = Jacobi-PCG in the persistent
+ * kernel (the default), 1 = flexible GMRES(restart) preconditioned by the
+ * hybrid Schwarz multigrid (Sec. 1, Sec. 3: GMRES + three-level HSMG with a
+ * CG + Jacobi coarse solve): levels N, 3, 1 (N, 2, 1 for N = 3, 4; N, 1 for
+ * N = 2), V-cycle in vcycle precision (SEM_F32 or SEM_F64), coarse PCG to
+ * relative tolerance 1e-2.  The pressure options' tol, abs_tol and maxit
+ * apply; their inner field does not (the V-cycle precision is vcycle).  With
+ * kind 1 every step launches directly (GMRES reads inner products back to the
+ * host), the projection (sem_tgv_set_projection) still applies, and the
+ * pressure entry of sem_tgv_diag counts GMRES iterations.  Synchronises the
+ * device; allocates the hierarchy (about 3 E-vectors per level, the coarser
+ * levels' contexts) and, on the first solve, 2 restart + 3 FP64 E-vectors.
+ * SEM_ERR_ARG: NULL tgv, kind outside 0..1, restart outside 1..64 or an
+ * unsupported vcycle; SEM_ERR_NOMEM. */
+SEM_API int sem_tgv_set_pressure_solver(sem_tgv *tgv, int kind, int restart, sem_dtype vcycle);
 
 /* Set the state at history level (0 = u^n, 1 = u^{n-1}, 2 = u^{n-2}) from
  * FP64 E-vectors u, v, w (and p for level 0; may be NULL), each device or host

@@ -43,6 +43,8 @@ int sem_pcg_solve_dev(sem_ctx *c, int slot, const double *b, double *x, double h
 int sem_pcg_solve_dev_batch(sem_ctx *c, int np, const double *const *b, double *const *x, double h1,
                             double h2, const sem_solve_opts &o, cudaStream_t s, int slot0);
 const void *sem_solve_state_ptr(const sem_ctx *c, int p, int *iters_off, int *status_off);
+int sem_gmres_solve_dev(sem_hsmg *H, int precond, const double *b_in, double *x, const sem_solve_opts &o,
+                        int m, sem_solve_info *info, cudaStream_t s);
 const void *sem_solve_sync_ptr(const sem_ctx *c);
 
 #define TGV_LOG 4096
@@ -82,6 +84,10 @@ struct sem_tgv {
     double hist_dt[2];        // sizes of the last two steps (most recent first)
     double cfl_target, dt_max; // adaptive step when cfl_target > 0
     TgvDev *hdev;             // pinned host copy of the counters
+    // pressure solver: 0 Jacobi-PCG (persistent kernel), 1 flexible GMRES + HSMG
+    int psolver, prestart;
+    sem_hsmg *hsmg;
+    sem_solve_info pinfo;     // the last GMRES pressure solve
     double *u[3][3], *C[3][3], *p, *unew[3], *F[3], *g[3], *bp, *rhs[3];
     // FP32 storage (rp = fp32): the velocity and convection histories live in
     // these FP32 buffers instead of u and C while storage == SEM_F32
@@ -693,6 +699,15 @@ __global__ void k_conv_f32_f64(const float *__restrict__ a, double *__restrict__
         b[t] = (double)a[t];
 }
 
+// Iterations and status of a solve known on the host (GMRES) into log slot `slot`.
+__global__ void k_tgv_log_host(TgvDev *dv, TgvLogEntry *log, int slot, int iters, int status, int reset)
+{
+    TgvLogEntry &L = log[dv->count % TGV_LOG];
+    if (reset) L.status = 0;
+    L.iters[slot] = iters;
+    if (status != 0 && L.status == 0) L.status = status;
+}
+
 // FP64 values as float pairs (hi = round(v), lo = round(v - hi)).
 __global__ void k_split_df64(const double *__restrict__ a, df64 *__restrict__ out, int64_t n)
 {
@@ -905,6 +920,17 @@ static int diag(sem_tgv *T, int advance, cudaStream_t s)
 static int pressure_projected(sem_tgv *T, cudaStream_t s);
 static void proj_free(sem_tgv *T);
 
+// The pressure Poisson solve A x = b (x holds the initial guess): Jacobi-PCG
+// in the persistent kernel (workspace slot 4), or flexible GMRES + HSMG (its
+// convergence status goes to the step's log, like the persistent solver's).
+static int pressure_solve(sem_tgv *T, const double *b, double *x, cudaStream_t s)
+{
+    if (!T->psolver) return sem_pcg_solve_dev(T->c, 4, b, x, 1.0, 0.0, T->po, s);
+    const int rc = sem_gmres_solve_dev(T->hsmg, 1, b, x, T->po, T->prestart, &T->pinfo, s);
+    if (rc == SEM_OK || rc == SEM_ERR_NOT_CONVERGED || rc == SEM_ERR_BREAKDOWN) return SEM_OK;
+    return rc;
+}
+
 // One step of order q on stream s (capturable).
 static int step_once(sem_tgv *T, int q, cudaStream_t s)
 {
@@ -947,7 +973,7 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     SEM_CHECK_LAUNCH();
     rc = sem_dssum_dev(c, T->bp, SEM_F64, s);
     if (rc) return rc;
-    rc = T->proj_max > 0 ? pressure_projected(T, s) : sem_pcg_solve_dev(c, 4, T->bp, T->p, 1.0, 0.0, T->po, s);
+    rc = T->proj_max > 0 ? pressure_projected(T, s) : pressure_solve(T, T->bp, T->p, s);
     if (rc) return rc;
     rc = round_stored(T, T->p, nL, s);
     if (rc) return rc;
@@ -956,7 +982,10 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     const char *st1 = (const char *)sem_solve_state_ptr(c, 1, &io, &so);
     const int stride = (int)(st1 - st0);
     const int *serr = (const int *)((const char *)sem_solve_sync_ptr(c) + 8);
-    k_tgv_log_iters<<<1, 32, 0, s>>>(st0, stride, io, so, serr, 0, 1, T->dev, T->log, 1);
+    if (T->psolver)
+        k_tgv_log_host<<<1, 1, 0, s>>>(T->dev, T->log, 0, T->pinfo.iters, T->pinfo.status, 1);
+    else
+        k_tgv_log_iters<<<1, 32, 0, s>>>(st0, stride, io, so, serr, 0, 1, T->dev, T->log, 1);
     SEM_CHECK_LAUNCH();
     // 5. velocity right-hand sides and the three Helmholtz solves from u^n
     VArgs va;
@@ -1025,6 +1054,7 @@ extern "C" void sem_tgv_destroy(sem_tgv *T)
     if (T->dev) cudaFree(T->dev);
     if (T->hlog) cudaFreeHost(T->hlog);
     if (T->hdev) cudaFreeHost(T->hdev);
+    sem_hsmg_destroy(T->hsmg);
     free(T);
 }
 
@@ -1351,7 +1381,7 @@ static int pressure_projected(sem_tgv *T, cudaStream_t s)
     SEM_CHECK_LAUNCH();
     // the remainder, from a zero guess
     SEM_CUDA(cudaMemsetAsync(T->pdx, 0, sizeof(double) * n, s));
-    if ((rc = sem_pcg_solve_dev(c, 4, T->pbq, T->pdx, 1.0, 0.0, T->po, s))) return rc;
+    if ((rc = pressure_solve(T, T->pbq, T->pdx, s))) return rc;
     k_vec_add<<<g, 256, 0, s>>>(T->p, T->pxb, T->pdx, n);
     SEM_CHECK_LAUNCH();
     // basis update: v = dx (or p after a restart), A v, CGS twice, A-normalise, append
@@ -1497,8 +1527,10 @@ static int advance(sem_tgv *T, int nsteps, cudaStream_t s)
     for (int it = 0; it < nsteps; ++it) {
         const int q = T->step + 1 < 3 ? T->step + 1 : 3;
         const bool adaptive = T->cfl_target > 0;
-        // graph replay only for third-order steps of one fixed size
-        const bool steady = q == 3 && !adaptive && T->hist_dt[0] == T->dt && T->hist_dt[1] == T->dt;
+        // graph replay only for third-order steps of one fixed size (and a
+        // pressure solver that does not read back to the host)
+        const bool steady = q == 3 && !adaptive && !T->psolver && T->hist_dt[0] == T->dt &&
+                            T->hist_dt[1] == T->dt;
         int rc = apply_policy(T, T->step + 1, s);
         if (rc) return rc;
         if (steady && s != 0 && T->graph_state == 0 && !T->graph_warm) {
@@ -1548,6 +1580,31 @@ static int advance(sem_tgv *T, int nsteps, cudaStream_t s)
             }
         }
     }
+    return SEM_OK;
+}
+
+extern "C" int sem_tgv_set_pressure_solver(sem_tgv *T, int kind, int restart, sem_dtype vcycle)
+{
+    if (!T || kind < 0 || kind > 1) return SEM_ERR_ARG;
+    if (kind == 1 && (restart < 1 || restart > 64 || (vcycle != SEM_F32 && vcycle != SEM_F64))) return SEM_ERR_ARG;
+    if (T->graph_state == 1) {
+        cudaGraphExecDestroy(T->graph);
+        T->graph_state = 0;
+    }
+    T->graph_warm = 0;
+    SEM_CUDA(cudaDeviceSynchronize());
+    sem_hsmg_destroy(T->hsmg);
+    T->hsmg = nullptr;
+    T->psolver = 0;
+    if (kind == 0) return SEM_OK;
+    // levels N, 3, 1 (N, 2, 1 for N = 3 or 4; N, 1 below)
+    const int N = T->c->N;
+    int orders[3] = {N, N >= 5 ? 3 : 2, 1}, nlev = N >= 3 ? 3 : (N == 2 ? 2 : 1);
+    if (nlev == 2) orders[1] = 1;
+    int rc = sem_hsmg_create(T->c, nlev, orders, 1.0, 0.0, vcycle, 1e-2, 200, &T->hsmg);
+    if (rc) return rc;
+    T->psolver = 1;
+    T->prestart = restart;
     return SEM_OK;
 }
 

@@ -102,14 +102,15 @@ def _errors(row, ref, uneven):
 
 
 def replay(configs=None, nel=32, N=7, re=1600.0, dt=1e-3, steps=200, warm=3, maxit=4000, projection=0,
-           cfl=None):
+           cfl=None, pressure="pcg"):
     """Run each configuration from the same initial state on cuda:0; returns a
     list of dicts with ms/step of the timed steps (CUDA events around the
     graph replays and one copy of the stepper's log), the GPU energy of those
     steps from NVML's counter (energy_j, None where the counter is not
     readable), mean velocity / pressure
     iterations, the worst status and the error metrics of its KE / enstrophy
-    history against A-0's.  cfl > 0 runs CFL-controlled steps from dt (one
+    history against A-0's.  pressure: "pcg" (Jacobi-PCG) or "gmres_hsmg" (the
+    paper's GMRES + HSMG; direct launches).  cfl > 0 runs CFL-controlled steps from dt (one
     host synchronisation and direct launches per step; the rows then carry the
     mean step and CFL of the timed steps).  The first `warm`
     steps (startup orders and the graph capture) are part of the history but
@@ -143,6 +144,8 @@ def replay(configs=None, nel=32, N=7, re=1600.0, dt=1e-3, steps=200, warm=3, max
         T.set_policy([rule(name)])
         if projection:
             T.set_projection(projection)
+        if pressure != "pcg":
+            T.set_pressure_solver(pressure)
         T.set(*ic)
         if cfl:
             T.set_dt(cfl_target=cfl)
@@ -186,11 +189,13 @@ def replay(configs=None, nel=32, N=7, re=1600.0, dt=1e-3, steps=200, warm=3, max
 
 
 def long_run(configs=("A-0", "A-1", "B-0"), nel=32, N=7, re=1600.0, dt=4e-3, t_end=12.0, projection=20,
-             chunk=250, warm=3, maxit=4000, every=25, budget_s=None, log=None, cfl=None, dt_max=None):
+             chunk=250, warm=3, maxit=4000, every=25, budget_s=None, log=None, cfl=None, dt_max=None,
+             pressure="pcg"):
     """Run each configuration from the Sec. 3 initial state to t_end (the long
     runs behind Table 3), in chunks of `chunk` graph-replayed steps; with
     cfl > 0 the steps are CFL-controlled from dt (Sec. 3 runs at CFL 0.4;
     capped by dt_max) and the run ends at the first step reaching t_end.
+    pressure: "pcg" (Jacobi-PCG) or "gmres_hsmg" (GMRES + HSMG, Sec. 3).
     Time- and energy-to-solution cover every step (CUDA events; NVML's energy
     counter around the run, None where it is not readable).  A run stops
     early when a solve fails to converge, KE or enstrophy stop being finite or
@@ -232,6 +237,8 @@ def long_run(configs=("A-0", "A-1", "B-0"), nel=32, N=7, re=1600.0, dt=4e-3, t_e
         T.set_policy([rule(name)])
         if projection:
             T.set_projection(projection)
+        if pressure != "pcg":
+            T.set_pressure_solver(pressure)
         T.set(*ic)
         if cfl:
             T.set_dt(cfl_target=cfl, dt_max=dt_max or 0.0)
@@ -285,7 +292,7 @@ def long_run(configs=("A-0", "A-1", "B-0"), nel=32, N=7, re=1600.0, dt=4e-3, t_e
         eps_ke = -np.gradient(ke, t) if len(t) > 2 else np.full_like(ke, np.nan)
         tp, ep = peak(t, en)
         out.append(dict(config=name, **TABLE2[name], re=re, dt=dt, nel=nel, N=N, projection=projection,
-                        cfl_target=cfl, steps=len(d), t_reached=float(t[-1]) if len(t) else 0.0, stopped=stop,
+                        cfl_target=cfl, pressure=pressure, steps=len(d), t_reached=float(t[-1]) if len(t) else 0.0, stopped=stop,
                         ms_per_step=ms / timed if timed else float("nan"),
                         time_to_solution_s=ms_all / 1e3, energy_j=joules, energy_reason=meter.reason,
                         dt_mean=float(np.mean([r["dt"] for r in d])) if d else float("nan"),
@@ -334,13 +341,14 @@ def main(argv=None):
     ap.add_argument("--cfl", type=float, default=None,
                     help="CFL-controlled steps from --dt towards this CFL number (Sec. 3: 0.4)")
     ap.add_argument("--dt-max", type=float, default=None)
+    ap.add_argument("--pressure", default="pcg", choices=["pcg", "gmres_hsmg"])
     ap.add_argument("--out", default=None, help="long runs: write the rows with their histories here")
     args = ap.parse_args(argv)
     if args.t_end is not None:
         rows = long_run(args.configs.split(","), args.nel, args.N, args.re, args.dt, args.t_end,
                         projection=args.projection or 20, budget_s=args.budget_s,
                         log=lambda m: print(m, file=sys.stderr, flush=True), cfl=args.cfl,
-                        dt_max=args.dt_max)
+                        dt_max=args.dt_max, pressure=args.pressure)
         if args.out:
             with open(args.out, "w") as f:
                 json.dump(rows, f)
@@ -348,7 +356,7 @@ def main(argv=None):
             print(json.dumps({k: v for k, v in r.items() if k != "series"}), flush=True)
         return
     rows = replay(args.configs.split(","), args.nel, args.N, args.re, args.dt, args.steps,
-                  projection=args.projection, cfl=args.cfl)
+                  projection=args.projection, cfl=args.cfl, pressure=args.pressure)
     for r in rows:
         r = {k: v for k, v in r.items() if k not in ("ke", "enstrophy", "t")}
         print(json.dumps(r))

@@ -74,7 +74,8 @@ EXPORTS = ["sem_setup", "sem_destroy", "sem_get_info", "sem_strerror", "sem_coor
            "sem_tgv_step", "sem_tgv_get", "sem_tgv_energy", "sem_tgv_destroy",
            "sem_pcg_solve_noalloc", "sem_device_status", "sem_tune_ax", "sem_set_ax_variant",
            "sem_tgv_set_policy", "sem_tgv_set_projection", "sem_tune_inner", "sem_set_inner_path",
-           "sem_tgv_set_dt"]
+           "sem_tgv_set_dt", "sem_hsmg_create", "sem_hsmg_apply", "sem_gmres_solve",
+           "sem_hsmg_destroy", "sem_tgv_set_pressure_solver"]
 
 
 def lib_path() -> str:
@@ -128,6 +129,15 @@ def load(build_if_missing: bool = True):
         L.sem_tgv_set_policy.argtypes = [vp, ctypes.c_int, ctypes.POINTER(TgvPolicy)]
         L.sem_tgv_set_projection.argtypes = [vp, ctypes.c_int]
         L.sem_tgv_set_dt.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.sem_hsmg_create.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      ctypes.POINTER(vp)]
+        L.sem_hsmg_apply.argtypes = [vp, vp, vp, vp]
+        L.sem_gmres_solve.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(SolveOpts), ctypes.c_int,
+                                      ctypes.POINTER(SolveInfo), vp]
+        L.sem_hsmg_destroy.argtypes = [vp]
+        L.sem_hsmg_destroy.restype = None
+        L.sem_tgv_set_pressure_solver.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.sem_tgv_destroy.restype = None
         L.sem_pcg_solve_noalloc.argtypes = [ctypes.c_int] * 4 + [ip, vp, vp, vp, ctypes.c_double,
                                                                  ctypes.c_double,
@@ -258,6 +268,42 @@ class Ctx:
         info = SolveInfo()
         _check(_lib.sem_last_solve_info(self._h, ctypes.byref(info)), "sem_last_solve_info")
         return info.as_dict()
+
+
+class HSMG:
+    """Hybrid Schwarz multigrid preconditioner and flexible GMRES on a context."""
+
+    def __init__(self, ctx, orders, h1=1.0, h2=0.0, dtype="f32", coarse_tol=1e-2, coarse_maxit=200):
+        self.ctx = ctx
+        o = (ctypes.c_int * len(orders))(*[int(v) for v in orders])
+        h = ctypes.c_void_p()
+        _check(_lib.sem_hsmg_create(ctx.handle, len(orders), o, float(h1), float(h2), DTYPES[dtype],
+                                    float(coarse_tol), int(coarse_maxit), ctypes.byref(h)),
+               "sem_hsmg_create")
+        self._h = h
+
+    def apply(self, r, z, stream=None):
+        _check(_lib.sem_hsmg_apply(self._h, ptr(r), ptr(z), _sp(r, stream)), "sem_hsmg_apply")
+
+    def gmres(self, b, x, restart=30, precond=True, stream=None, **kw):
+        o = opts(**kw)
+        info = SolveInfo()
+        rc = _lib.sem_gmres_solve(self._h, int(bool(precond)), ptr(b), ptr(x), ctypes.byref(o),
+                                  int(restart), ctypes.byref(info), _sp(b, stream))
+        if rc not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(rc, "sem_gmres_solve")
+        return info.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.sem_hsmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _sp(t, stream):
@@ -410,6 +456,13 @@ class TGV:
         by dt_max > 0; 0 keeps the step fixed)."""
         _check(_lib.sem_tgv_set_dt(self._h, float(dt), float(cfl_target), float(dt_max)),
                "sem_tgv_set_dt")
+
+    def set_pressure_solver(self, kind="gmres_hsmg", restart=30, vcycle="f32"):
+        """Pressure solver: "pcg" (Jacobi-PCG, the default) or "gmres_hsmg" (flexible
+        GMRES with the hybrid Schwarz multigrid, V-cycle in `vcycle` precision)."""
+        k = {"pcg": 0, "gmres_hsmg": 1}[kind]
+        _check(_lib.sem_tgv_set_pressure_solver(self._h, k, int(restart), DTYPES[vcycle]),
+               "sem_tgv_set_pressure_solver")
 
     def set(self, u, v, w, p=None, level=0, step=0, t=0.0, stream=None):
         _check(_lib.sem_tgv_set(self._h, level, ptr(u), ptr(v), ptr(w), ptr(p), step, t,
