@@ -343,9 +343,12 @@ SEM_API int sem_hsmg_apply(sem_hsmg *hsmg, const double *r, double *z, void *str
  * FP64 E-vectors, allocated on first use and kept).  Synchronises the stream
  * (the host solves the Hessenberg least-squares problem and reads three
  * inner-product sets per iteration).  Converged (SEM_OK) when the true
- * residual, or the Arnoldi estimate of a cycle, meets the target; the true
- * residual then may exceed it by the operator's rounding floor (the
- * FP64-accurate operator's relative error, a few 1e-13, times ||A|| ||x||).
+ * residual, computed at the end of every cycle, meets the target; below
+ * 1e-8 ||b|| it is computed with the native FP64 operator (the FP64-accurate
+ * operator's rounding floor, a few 1e-13 relative per application times
+ * ||A|| ||x||, can reach that level), so that the cycles act as the inner
+ * solves of an FP64 refinement.  A cycle that meets its own Arnoldi estimate
+ * without halving the true residual ends the solve (SEM_ERR_NOT_CONVERGED).
  * info: iters (GMRES iterations), outer_iters (restarts), final_rnorm (true
  * residual), bnorm.  Returns info->status (SEM_OK, SEM_ERR_NOT_CONVERGED,
  * SEM_ERR_BREAKDOWN) or an error. */

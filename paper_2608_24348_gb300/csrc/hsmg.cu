@@ -778,9 +778,15 @@ int sem_gmres_solve_dev(sem_hsmg *H, int precond, const double *b_in, double *x,
     if ((rc = hs_dots(H, r, r, n, 1, s))) return rc;
     const double bnorm = sqrt(H->hdots[0]);
     const double target = o.abs_tol ? o.tol : o.tol * bnorm;
+    // The true residual decides convergence.  Below 1e-8 ||b|| it is taken
+    // with the native FP64 operator: the FP64-accurate operator's rounding
+    // floor (a few 1e-13 relative per application, times ||A|| ||x||) can
+    // reach that level, and GMRES cycles on the fast operator then act as the
+    // inner solves of an FP64 refinement.
+    const bool native_res = tight || target < 1e-8 * bnorm;
     auto true_residual = [&](double *beta) -> int {
         // r = b' - A x
-        int rc2 = hs_op(H, x, w, tight, s);
+        int rc2 = hs_op(H, x, w, native_res, s);
         if (rc2) return rc2;
         SEM_CUDA(cudaMemcpyAsync(r, b_in, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         if (singular) {
@@ -803,6 +809,8 @@ int sem_gmres_solve_dev(sem_hsmg *H, int precond, const double *b_in, double *x,
     std::vector<double> Hm((size_t)(m + 1) * m), cs(m + 1), sn(m + 1), g(m + 1), y(m), h(m + 1);
     bool estimate_met = false;
     while (status == SEM_ERR_NOT_CONVERGED && it < o.maxit) {
+        const double beta0 = beta;
+        estimate_met = false;
         k_hs_scale<<<hs_grid(n), 256, 0, s>>>(V, r, 1.0 / beta, n);
         SEM_CHECK_LAUNCH();
         std::fill(g.begin(), g.end(), 0.0);
@@ -861,10 +869,10 @@ int sem_gmres_solve_dev(sem_hsmg *H, int precond, const double *b_in, double *x,
         if ((rc = true_residual(&beta))) return rc;
         if (broke) break;
         if (!isfinite(beta)) { status = SEM_ERR_BREAKDOWN; break; }
-        // converged when the true residual, or the Arnoldi estimate of the
-        // cycle, meets the target (the true residual of the FP64-accurate
-        // operator has a rounding floor that the estimate does not see)
-        if (beta <= target || estimate_met) { status = SEM_OK; break; }
+        if (beta <= target) { status = SEM_OK; break; }
+        // a cycle that met its own estimate without halving the true residual
+        // has reached the floor of the operators: stop there
+        if (estimate_met && beta > 0.5 * beta0) break;
         ++restarts;
     }
     if (singular) {  // remove the B-weighted mean of x
