@@ -171,6 +171,8 @@ SEM_API int sem_ax(sem_ctx *ctx, const void *u, void *w, double h1, double h2, s
  *    9 and 10 = as 8 with register budgets for 20 and 24 warps per SM
  *    (the staged forms fall back to 3 or 4 for u in host memory or not
  *    16-byte aligned);
+ *  - SEM_F64_NATIVE with even N+1: 0 = the folded (even-odd) kernel,
+ *    1 = the unfolded kernel;
  *  - other cases have one candidate, reported as 0 ms. */
 SEM_API int sem_tune_ax(sem_ctx *ctx, sem_dtype dtype, int reps, double *ms, int *best);
 
@@ -458,7 +460,7 @@ SEM_API int sem_tgv_set_dt(sem_tgv *tgv, double dt, double cfl_target, double dt
  * hybrid Schwarz multigrid (Sec. 1, Sec. 3: GMRES + three-level HSMG with a
  * CG + Jacobi coarse solve): levels N, 3, 1 (N, 2, 1 for N = 3, 4; N, 1 for
  * N = 2), V-cycle in vcycle precision (SEM_F32 or SEM_F64), coarse PCG to
- * relative tolerance 1e-2.  The pressure options' tol, abs_tol and maxit
+ * relative tolerance 0.1.  The pressure options' tol, abs_tol and maxit
  * apply; their inner field does not (the V-cycle precision is vcycle).  With
  * kind 1 every step launches directly (GMRES reads inner products back to the
  * host), the projection (sem_tgv_set_projection) still applies, and the

@@ -19,7 +19,8 @@
 // GMRES vectors, its operator (the FP64-accurate one of sem_ax) and its inner
 // products (sum_local a b / mult) are FP64.  GMRES is right preconditioned and
 // flexible (x = x0 + Z y), restarted after m steps, with classical
-// Gram-Schmidt applied twice and Givens rotations; the small Hessenberg
+// Gram-Schmidt (a second pass where the first cancelled) and Givens
+// rotations; the small Hessenberg
 // problem is solved on the host, which reads the inner products back each
 // iteration.
 #include <math.h>
@@ -37,7 +38,7 @@ int sem_pcg_solve_dev(sem_ctx *c, int slot, const double *b, double *x, double h
                       const sem_solve_opts &o, cudaStream_t s);
 
 #define HS_MAXLEV 3
-#define HS_DOT_BLOCKS 304   // 2 x 152 SMs; fixed so that the sums are deterministic
+#define HS_DOT_BLOCKS 1216  // 8 x 152 SMs; fixed so that the sums are deterministic
 #define HS_DOT_K 8          // inner products per pass over the data
 
 // ---------------------------------------------------------------------------
@@ -295,7 +296,24 @@ __global__ void k_hs_dots(const double *__restrict__ w, const double *__restrict
     double acc[HS_DOT_K];
 #pragma unroll
     for (int i = 0; i < HS_DOT_K; ++i) acc[i] = 0.0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // four grid strides per pass, every load of a pass issued before its use
+    for (; t + 3 * G < n; t += 4 * G) {
+        double a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = w[t + q * G] * imult[t + q * G];
+#pragma unroll
+        for (int i = 0; i < HS_DOT_K; ++i)
+            if (i < k) {
+                double v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = V ? V[i * ld + t + q * G] : 1.0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[i] = fma(a[q], v[q], acc[i]);
+            }
+    }
+    for (; t < n; t += G) {
         const double a = w[t] * imult[t];
 #pragma unroll
         for (int i = 0; i < HS_DOT_K; ++i)
@@ -699,18 +717,30 @@ extern "C" int sem_hsmg_apply(sem_hsmg *H, const double *r, double *z, void *str
 // ---------------------------------------------------------------------------
 
 // dots[i] = <w, v_i>, i < k (V == nullptr: <w, 1>), into H->hdots (synchronises s).
-static int hs_dots(sem_hsmg *H, const double *w, const double *V, int64_t ld, int k, cudaStream_t s)
+// (enqueue only: the values land in H->dots + at)
+static int hs_dots_enq(sem_hsmg *H, const double *w, const double *V, int64_t ld, int k, int at, cudaStream_t s)
 {
     const int64_t n = H->L[0].c->nL;
     for (int i0 = 0; i0 < k; i0 += HS_DOT_K) {
         const int kk = k - i0 < HS_DOT_K ? k - i0 : HS_DOT_K;
         k_hs_dots<<<HS_DOT_BLOCKS, 256, 0, s>>>(w, V ? V + i0 * ld : nullptr, ld, kk, H->imult64, H->part, n);
-        k_hs_dot_final<<<1, 32, 0, s>>>(H->part, kk, HS_DOT_BLOCKS, H->dots + i0);
+        k_hs_dot_final<<<1, 32, 0, s>>>(H->part, kk, HS_DOT_BLOCKS, H->dots + at + i0);
         SEM_CHECK_LAUNCH();
     }
+    return SEM_OK;
+}
+
+static int hs_dots_read(sem_hsmg *H, int k, cudaStream_t s)
+{
     SEM_CUDA(cudaMemcpyAsync(H->hdots, H->dots, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
     SEM_CUDA(cudaStreamSynchronize(s));
     return SEM_OK;
+}
+
+static int hs_dots(sem_hsmg *H, const double *w, const double *V, int64_t ld, int k, cudaStream_t s)
+{
+    int rc = hs_dots_enq(H, w, V, ld, k, 0, s);
+    return rc ? rc : hs_dots_read(H, k, s);
 }
 
 // y += sum_i c[i] v_i
@@ -825,19 +855,28 @@ int sem_gmres_solve_dev(sem_hsmg *H, int precond, const double *b_in, double *x,
                 SEM_CUDA(cudaMemcpyAsync(zj, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
             }
             if ((rc = hs_op(H, zj, w, tight, s))) return rc;
-            // classical Gram-Schmidt, twice
+            // classical Gram-Schmidt; a second pass only when the first removed
+            // more than half of |w|^2 ("twice is enough": the first pass's
+            // projections lost accuracy to cancellation)
             std::fill(h.begin(), h.end(), 0.0);
+            double hn = 0.0;
             for (int pass = 0; pass < 2; ++pass) {
-                if ((rc = hs_dots(H, w, V, n, j + 1, s))) return rc;
+                if ((rc = hs_dots_enq(H, w, V, n, j + 1, 0, s))) return rc;
+                if ((rc = hs_dots_enq(H, w, w, n, 1, j + 1, s))) return rc;
+                if ((rc = hs_dots_read(H, j + 2, s))) return rc;
+                const double ww = H->hdots[j + 1];
                 std::vector<double> neg(j + 1);
+                double proj = 0.0;
                 for (int i = 0; i <= j; ++i) {
                     h[i] += H->hdots[i];
                     neg[i] = -H->hdots[i];
+                    proj += H->hdots[i] * H->hdots[i];
                 }
                 if ((rc = hs_maxpy(H, w, V, n, j + 1, neg.data(), s))) return rc;
+                if (ww - proj > 0.5 * ww) break;
             }
             if ((rc = hs_dots(H, w, w, n, 1, s))) return rc;
-            const double hn = sqrt(H->hdots[0]);
+            hn = sqrt(H->hdots[0]);
             for (int i = 0; i <= j; ++i) Hm[(size_t)i * m + j] = h[i];
             for (int i = 0; i < j; ++i) {  // earlier rotations on column j
                 const double a = Hm[(size_t)i * m + j], b2 = Hm[(size_t)(i + 1) * m + j];

@@ -8,6 +8,8 @@ int sem_ax_tc(sem_ctx *c, const float *u, float *w, double h1, double h2, int fp
               cudaStream_t s);  // ax_tc.cu
 int sem_ax_tc_split(sem_ctx *c, const float *u, float *w, double h1, double h2, int fp16,
                     cudaStream_t s);  // ax_tc.cu
+int sem_launch_ax_f64_v(const sem_ctx *c, const double *u, double *w, double h1, double h2, int fold,
+                        cudaStream_t s);
 int sem_launch_ax_f64(const sem_ctx *c, const double *u, double *w, double h1, double h2,
                       cudaStream_t s);  // ax_f64.cu
 int sem_launch_ax_f32_variant(const sem_ctx *c, int variant, const float *u, float *w, float h1,
@@ -26,7 +28,7 @@ int sem_launch_ax_df(const sem_ctx *c, const double *u, double *w, double h1, do
 // latter also with register budgets for 20 (9) and 24 (10) warps per SM.
 #define SEM_NVARIANT 11
 static_assert(SEM_NVARIANT <= SEM_TUNE_MAX, "tuner output array");
-static int sem_nvariant(sem_dtype dt) { return dt == SEM_F64 ? 11 : dt == SEM_F32 ? 3 : 1; }
+static int sem_nvariant(sem_dtype dt) { return dt == SEM_F64 ? 11 : dt == SEM_F32 ? 3 : dt == SEM_F64_NATIVE ? 2 : 1; }
 static int g_variant[SEM_NMAX + 1][5];  // 0 = not set -> built-in default
 static int g_variant_set[SEM_NMAX + 1][5];
 
@@ -82,7 +84,8 @@ int sem_ax_dev(sem_ctx *c, const void *u, void *w, double h1, double h2, sem_dty
     if (dt == SEM_F64) {
         return sem_launch_ax_df(c, (const double *)u, (double *)w, h1, h2, s);
     } else if (dt == SEM_F64_NATIVE) {
-        return sem_launch_ax_f64(c, (const double *)u, (double *)w, h1, h2, s);
+        return sem_launch_ax_f64_v(c, (const double *)u, (double *)w, h1, h2,
+                                   sem_ax_variant(c->N, SEM_F64_NATIVE) == 0, s);
     } else if (dt == SEM_F32) {
         return sem_launch_ax_f32_variant(c, sem_ax_variant(c->N, SEM_F32), (const float *)u, (float *)w,
                                          (float)h1, (float)h2, s);
@@ -379,7 +382,10 @@ extern "C" int sem_tune_ax(sem_ctx *c, sem_dtype dt, int reps, double *ms, int *
     if (reps < 1) reps = 5;
     // FP32: three tile shapes; FP64-accurate, even N+1 <= 10: three elements-per-block
     // counts of the folded kernel; otherwise one candidate
-    const int nvar = dt == SEM_F32 || (dt == SEM_F64 && c->n % 2 == 0 && c->n <= 12) ? sem_nvariant(dt) : 1;
+    const int nvar = dt == SEM_F32 || (dt == SEM_F64 && c->n % 2 == 0 && c->n <= 12) ||
+                             (dt == SEM_F64_NATIVE && c->n % 2 == 0)
+                         ? sem_nvariant(dt)
+                         : 1;
     if (ms)
         for (int v = 0; v < SEM_NVARIANT; ++v) ms[v] = -1.0;
     if (nvar == 1) {
@@ -403,6 +409,8 @@ extern "C" int sem_tune_ax(sem_ctx *c, sem_dtype dt, int reps, double *ms, int *
     auto run = [&](int v) {
         if (dt == SEM_F32)
             return sem_launch_ax_f32_variant(c, v, (const float *)u, (float *)w, 1.0f, 1.0f, s);
+        if (dt == SEM_F64_NATIVE)
+            return sem_launch_ax_f64_v(c, (const double *)u, (double *)w, 1.0, 1.0, v == 0, s);
         int rc = sem_set_ax_variant(c->N, dt, v);
         return rc ? rc : sem_launch_ax_df(c, (const double *)u, (double *)w, 1.0, 1.0, s);
     };

@@ -1601,7 +1601,7 @@ extern "C" int sem_tgv_set_pressure_solver(sem_tgv *T, int kind, int restart, se
     const int N = T->c->N;
     int orders[3] = {N, N >= 5 ? 3 : 2, 1}, nlev = N >= 3 ? 3 : (N == 2 ? 2 : 1);
     if (nlev == 2) orders[1] = 1;
-    int rc = sem_hsmg_create(T->c, nlev, orders, 1.0, 0.0, vcycle, 1e-2, 200, &T->hsmg);
+    int rc = sem_hsmg_create(T->c, nlev, orders, 1.0, 0.0, vcycle, 0.1, 200, &T->hsmg);
     if (rc) return rc;
     T->psolver = 1;
     T->prestart = restart;

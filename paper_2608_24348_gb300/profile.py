@@ -2,8 +2,11 @@
 
     python -m paper_2608_24348_gb300.profile --kernel ax_f64 --nel 24 --reps 3
 
-Kernels: ax_f64, ax_f32, ax_bf16_tc, dssum, pcg_f64, pcg_f32 (a bounded number
-of PCG iterations), tgv_f64, tgv_f32 (steps of the Taylor-Green stepper).
+Kernels: ax_f64, ax_f64_native, ax_f32, ax_bf16_tc, dssum, pcg_f64, pcg_f32 (a
+bounded number of PCG iterations), gmres_hsmg (a bounded number of GMRES
+iterations with the hybrid Schwarz multigrid, FP32 V-cycle), tgv_f64, tgv_f32
+(steps of the Taylor-Green stepper; --gmres for the GMRES + HSMG pressure
+solve).
 The mesh is the benchmark's: nel^3 elements, order N, interior vertices
 perturbed by up to 10%.  --variant selects sem_ax's kernel candidate for the
 order and dtype (see sem_tune_ax; default: the built-in choice).
@@ -23,6 +26,7 @@ def main(argv=None):
     ap.add_argument("--maxit", type=int, default=20)
     ap.add_argument("--projection", type=int, default=0, help="TGV: pressure projection space")
     ap.add_argument("--variant", type=int, default=-1, help="sem_ax kernel candidate (-1: default)")
+    ap.add_argument("--gmres", action="store_true", help="TGV: GMRES + HSMG pressure solver")
     args = ap.parse_args(argv)
 
     import json
@@ -41,7 +45,7 @@ def main(argv=None):
         dt = args.kernel[3:] if args.kernel.startswith("ax") else "f64"
         if args.variant >= 0:
             sem.set_ax_variant(args.N, dt, args.variant)
-        x = u if dt == "f64" else u.float()
+        x = u if dt.startswith("f64") else u.float()
         w = torch.empty_like(x)
         for _ in range(args.reps):
             if args.kernel == "dssum":
@@ -56,6 +60,14 @@ def main(argv=None):
             x = torch.zeros_like(b)
             ctx.pcg_solve(b, x, 1.0, 0.0, tol=1e-14, maxit=args.maxit,
                           inner=args.kernel[4:], inner_tol=1e-4)
+    elif args.kernel == "gmres_hsmg":
+        b = torch.empty_like(u)
+        ctx.ax(u, b, 0.0, 1.0, "f64")
+        ctx.dssum(b, "f64")
+        H = sem.HSMG(ctx, [args.N, 3, 1], dtype="f32", coarse_tol=0.1)
+        for _ in range(args.reps):
+            x = torch.zeros_like(b)
+            H.gmres(b, x, restart=30, tol=1e-14, maxit=args.maxit)
     elif tgv:
         x, y, z = torch.empty(3 * ctx.nL, dtype=torch.float64, device=dev).view(3, -1)
         xyz = torch.empty(3 * ctx.nL, dtype=torch.float64, device=dev)
@@ -65,6 +77,8 @@ def main(argv=None):
         T = sem.TGV(ctx, 1.0 / 1600, 1e-3, op=args.kernel[4:])
         if args.projection:
             T.set_projection(args.projection)
+        if args.gmres:
+            T.set_pressure_solver("gmres_hsmg")
         T.set(uu.contiguous(), vv.contiguous(), (ww + 0 * x).contiguous(), pp.contiguous())
         T.step(3)  # startup orders 1, 2 and the first third-order step (graph capture)
         torch.cuda.synchronize()

@@ -273,7 +273,7 @@ class Ctx:
 class HSMG:
     """Hybrid Schwarz multigrid preconditioner and flexible GMRES on a context."""
 
-    def __init__(self, ctx, orders, h1=1.0, h2=0.0, dtype="f32", coarse_tol=1e-2, coarse_maxit=200):
+    def __init__(self, ctx, orders, h1=1.0, h2=0.0, dtype="f32", coarse_tol=0.1, coarse_maxit=200):
         self.ctx = ctx
         o = (ctypes.c_int * len(orders))(*[int(v) for v in orders])
         h = ctypes.c_void_p()

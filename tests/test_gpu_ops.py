@@ -331,3 +331,30 @@ def test_dssum_full_size(sem):
     # oracle-free closed check: sum of copies by unique index (numpy bincount)
     ref = np.bincount(m_idx, weights=u)[m_idx]
     assert np.abs(ud.cpu().numpy() - ref).max() <= 64 * 2.3e-16
+
+
+@pytest.mark.parametrize("N,nel", [(1, (3, 4, 2)), (2, (3, 3, 3)), (4, (3, 2, 4)), (7, (4, 3, 3)),
+                                   (9, (2, 3, 2)), (15, (2, 2, 1))])
+def test_native_f64_operator_matches_oracle(sem, N, nel):
+    """The native FP64 operator (the folded even-odd kernel for even N+1, the
+    unfolded one otherwise) within 1e-13 of the oracle on a deformed mesh; for
+    even N+1 both candidates agree to FP64 rounding and the tuner times both."""
+    torch, dev = torch_dev()
+    ctx, m, _ = make(sem, N, nel, 0.1)
+    u = inputs.local_uniform_field(ctx.nL, seed=21)
+    ref = m.ax(u, 0.4, 3.0)
+    ud = torch.from_numpy(u).to(dev)
+    outs = []
+    nvar = 2 if (N + 1) % 2 == 0 else 1
+    for v in range(nvar):
+        sem.set_ax_variant(N, "f64_native", v)
+        wd = torch.empty_like(ud)
+        ctx.ax(ud, wd, 0.4, 3.0, "f64_native")
+        outs.append(wd.cpu().numpy())
+        assert rel_err(outs[-1], ref) <= 1e-13, (N, v, rel_err(outs[-1], ref))
+    if nvar == 2:
+        assert rel_err(outs[0], outs[1]) <= 1e-14
+        r = sem.autotune(ctx, "f64_native")
+        assert r["variant"] in (0, 1) and min(r["ms"][:2]) > 0, r
+    sem.set_ax_variant(N, "f64_native", -1)
+    assert ctx.device_status() == 0
