@@ -334,12 +334,21 @@ __global__ void k_hs_dots(const double *__restrict__ w, const double *__restrict
     }
 }
 
-__global__ void k_hs_dot_final(const double *__restrict__ part, int k, int nb, double *__restrict__ out)
+// One block per value: a fixed strided split of the nb partials over the
+// threads, then a fixed tree (blockDim.x a power of two).
+__global__ void k_hs_dot_final(const double *__restrict__ part, int nb, double *__restrict__ out)
 {
-    if (threadIdx.x >= k) return;
+    __shared__ double red[256];
+    const double *p = part + (size_t)blockIdx.x * nb;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[threadIdx.x * nb + b];
-    out[threadIdx.x] = s;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += p[b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
 }
 
 // y += sum_i c_i v_i for up to 16 vectors v_i = V + i*ld
@@ -724,7 +733,7 @@ static int hs_dots_enq(sem_hsmg *H, const double *w, const double *V, int64_t ld
     for (int i0 = 0; i0 < k; i0 += HS_DOT_K) {
         const int kk = k - i0 < HS_DOT_K ? k - i0 : HS_DOT_K;
         k_hs_dots<<<HS_DOT_BLOCKS, 256, 0, s>>>(w, V ? V + i0 * ld : nullptr, ld, kk, H->imult64, H->part, n);
-        k_hs_dot_final<<<1, 32, 0, s>>>(H->part, kk, HS_DOT_BLOCKS, H->dots + at + i0);
+        k_hs_dot_final<<<kk, 256, 0, s>>>(H->part, HS_DOT_BLOCKS, H->dots + at + i0);
         SEM_CHECK_LAUNCH();
     }
     return SEM_OK;
@@ -916,7 +925,7 @@ int sem_gmres_solve_dev(sem_hsmg *H, int precond, const double *b_in, double *x,
     }
     if (singular) {  // remove the B-weighted mean of x
         k_hs_bsum<<<HS_DOT_BLOCKS, 256, 0, s>>>(x, c->geo64, c->n * c->n * c->n, c->E, H->part);
-        k_hs_dot_final<<<1, 32, 0, s>>>(H->part, 2, HS_DOT_BLOCKS, H->dots);
+        k_hs_dot_final<<<2, 256, 0, s>>>(H->part, HS_DOT_BLOCKS, H->dots);
         SEM_CHECK_LAUNCH();
         SEM_CUDA(cudaMemcpyAsync(H->hdots, H->dots, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
         SEM_CUDA(cudaStreamSynchronize(s));
