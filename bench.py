@@ -398,6 +398,7 @@ def tgv_replay_section(steps=200):
     and the Sec. 4.2 errors of A-1's KE / enstrophy history against A-0's."""
     from paper_2608_24348_gb300 import policy
     rows = policy.replay(configs=["A-0", "A-1"], steps=steps, projection=20)
+    ref = rows[0]
     out = {"workload": f"TGV Re=1600, 32^3 undeformed, N=7, dt=1e-3, {steps} steps, projection 20, "
                        "BDF3/EXT3 with 3/2 dealiasing; ms per graph-replayed step after 3; GPU "
                        "energy of those steps from NVML's counter"}
@@ -411,6 +412,13 @@ def tgv_replay_section(steps=200):
                                            if r["energy_j"] is not None else None)}
         if r["energy_j"] is None:
             out[r["config"]]["energy_unavailable"] = r["energy_reason"]
+    # the paper's pressure solver (GMRES + HSMG) in the same A-0 run: direct
+    # launches (GMRES reads back to the host), errors against the Jacobi-PCG run
+    g = policy.replay(configs=["A-0"], steps=steps, projection=20, pressure="gmres_hsmg")[0]
+    out["A-0_gmres_hsmg"] = {"ms_per_step": g["ms_per_step"], "pres_iters": g["pres_iters"],
+                             "vel_iters": g["vel_iters"], "status": g["status"], "energy_j": g["energy_j"],
+                             "e_E_max_vs_pcg": policy.e_max(g["ke"], ref["ke"]),
+                             "e_Omega_max_vs_pcg": policy.e_max(g["enstrophy"], ref["enstrophy"])}
     # CFL-controlled steps (Sec. 3: CFL 0.4) from the same state: one host
     # synchronisation and direct launches per step
     n_cfl = max(20, steps // 2)
