@@ -794,8 +794,9 @@ static int hs_op(sem_hsmg *H, const double *x, double *y, bool tight, cudaStream
     return sem_dssum_dev(c, y, SEM_F64, s);
 }
 
+// x_zero != 0: the caller guarantees x = 0 on entry (the first residual is b').
 int sem_gmres_solve_dev(sem_hsmg *H, int precond, const double *b_in, double *x, const sem_solve_opts &o,
-                        int m, sem_solve_info *info, cudaStream_t s)
+                        int m, sem_solve_info *info, cudaStream_t s, int x_zero)
 {
     sem_ctx *c = H->L[0].c;
     const int64_t n = c->nL;
@@ -809,9 +810,11 @@ int sem_gmres_solve_dev(sem_hsmg *H, int precond, const double *b_in, double *x,
     double *r = H->r, *w = H->w, *V = H->V, *Z = H->Z;
     // b' = b minus its mean over unique nodes when the operator is singular (r holds b')
     SEM_CUDA(cudaMemcpyAsync(r, b_in, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    double bmean = 0.0;
     if (singular) {
         if ((rc = hs_dots(H, r, nullptr, 0, 1, s))) return rc;
-        k_hs_add_scalar<<<hs_grid(n), 256, 0, s>>>(r, -H->hdots[0] / (double)c->nG, n);
+        bmean = H->hdots[0] / (double)c->nG;
+        k_hs_add_scalar<<<hs_grid(n), 256, 0, s>>>(r, -bmean, n);
         SEM_CHECK_LAUNCH();
     }
     if ((rc = hs_dots(H, r, r, n, 1, s))) return rc;
@@ -829,8 +832,7 @@ int sem_gmres_solve_dev(sem_hsmg *H, int precond, const double *b_in, double *x,
         if (rc2) return rc2;
         SEM_CUDA(cudaMemcpyAsync(r, b_in, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         if (singular) {
-            if ((rc2 = hs_dots(H, r, nullptr, 0, 1, s))) return rc2;
-            k_hs_add_scalar<<<hs_grid(n), 256, 0, s>>>(r, -H->hdots[0] / (double)c->nG, n);
+            k_hs_add_scalar<<<hs_grid(n), 256, 0, s>>>(r, -bmean, n);
             SEM_CHECK_LAUNCH();
         }
         k_hs_sub<double><<<hs_grid(n), 256, 0, s>>>(w, r, n);  // w = r - w
@@ -840,8 +842,8 @@ int sem_gmres_solve_dev(sem_hsmg *H, int precond, const double *b_in, double *x,
         *beta = sqrt(H->hdots[0]);
         return SEM_OK;
     };
-    double beta;
-    if ((rc = true_residual(&beta))) return rc;
+    double beta = bnorm;  // x = 0: the first residual is b' (already in r)
+    if (!x_zero && (rc = true_residual(&beta))) return rc;
     int it = 0, restarts = 0, status = SEM_ERR_NOT_CONVERGED;
     if (!isfinite(beta) || !isfinite(bnorm)) status = SEM_ERR_BREAKDOWN;
     else if (beta <= target) status = SEM_OK;
@@ -947,5 +949,5 @@ extern "C" int sem_gmres_solve(sem_hsmg *H, int precond, const double *b, double
 {
     if (!H || !b || !x || !opts || !info) return SEM_ERR_ARG;
     if (!sem_is_device_ptr(b) || !sem_is_device_ptr(x)) return SEM_ERR_ARG;
-    return sem_gmres_solve_dev(H, precond, b, x, *opts, restart, info, (cudaStream_t)stream);
+    return sem_gmres_solve_dev(H, precond, b, x, *opts, restart, info, (cudaStream_t)stream, 0);
 }

@@ -44,7 +44,7 @@ int sem_pcg_solve_dev_batch(sem_ctx *c, int np, const double *const *b, double *
                             double h2, const sem_solve_opts &o, cudaStream_t s, int slot0);
 const void *sem_solve_state_ptr(const sem_ctx *c, int p, int *iters_off, int *status_off);
 int sem_gmres_solve_dev(sem_hsmg *H, int precond, const double *b_in, double *x, const sem_solve_opts &o,
-                        int m, sem_solve_info *info, cudaStream_t s);
+                        int m, sem_solve_info *info, cudaStream_t s, int x_zero);
 const void *sem_solve_sync_ptr(const sem_ctx *c);
 
 #define TGV_LOG 4096
@@ -923,10 +923,10 @@ static void proj_free(sem_tgv *T);
 // The pressure Poisson solve A x = b (x holds the initial guess): Jacobi-PCG
 // in the persistent kernel (workspace slot 4), or flexible GMRES + HSMG (its
 // convergence status goes to the step's log, like the persistent solver's).
-static int pressure_solve(sem_tgv *T, const double *b, double *x, cudaStream_t s)
+static int pressure_solve(sem_tgv *T, const double *b, double *x, int x_zero, cudaStream_t s)
 {
     if (!T->psolver) return sem_pcg_solve_dev(T->c, 4, b, x, 1.0, 0.0, T->po, s);
-    const int rc = sem_gmres_solve_dev(T->hsmg, 1, b, x, T->po, T->prestart, &T->pinfo, s);
+    const int rc = sem_gmres_solve_dev(T->hsmg, 1, b, x, T->po, T->prestart, &T->pinfo, s, x_zero);
     if (rc == SEM_OK || rc == SEM_ERR_NOT_CONVERGED || rc == SEM_ERR_BREAKDOWN) return SEM_OK;
     return rc;
 }
@@ -973,7 +973,7 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     SEM_CHECK_LAUNCH();
     rc = sem_dssum_dev(c, T->bp, SEM_F64, s);
     if (rc) return rc;
-    rc = T->proj_max > 0 ? pressure_projected(T, s) : pressure_solve(T, T->bp, T->p, s);
+    rc = T->proj_max > 0 ? pressure_projected(T, s) : pressure_solve(T, T->bp, T->p, 0, s);
     if (rc) return rc;
     rc = round_stored(T, T->p, nL, s);
     if (rc) return rc;
@@ -1381,7 +1381,7 @@ static int pressure_projected(sem_tgv *T, cudaStream_t s)
     SEM_CHECK_LAUNCH();
     // the remainder, from a zero guess
     SEM_CUDA(cudaMemsetAsync(T->pdx, 0, sizeof(double) * n, s));
-    if ((rc = pressure_solve(T, T->pbq, T->pdx, s))) return rc;
+    if ((rc = pressure_solve(T, T->pbq, T->pdx, 1, s))) return rc;
     k_vec_add<<<g, 256, 0, s>>>(T->p, T->pxb, T->pdx, n);
     SEM_CHECK_LAUNCH();
     // basis update: v = dx (or p after a restart), A v, CGS twice, A-normalise, append
