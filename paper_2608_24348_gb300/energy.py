@@ -2,7 +2,7 @@
 
 Energy-to-solution (Sec. 4, Table 3) is the energy a run draws; here it is
 the difference of the device's cumulative energy counter (millijoules since
-the driver loaded) around the run, for the GPU that runs it.  Only NVML's
+the GPU's kernel module loaded) around the run, for the GPU that runs it.  Only NVML's
 query calls are made: nothing is set, locked or reset.  The library is
 loaded through ctypes (no Python NVML package is needed); a missing
 library, an unsupported counter or any NVML error leaves the meter
