@@ -157,3 +157,36 @@ def test_stepper_with_gmres_pressure_matches_oracle(sem):
     assert rel([r["enstrophy"] for r in d], ref[:, 2]) <= 1e-8
     its = [r["iters"][0] for r in d]
     assert max(its[3:]) <= 25 and np.mean(its) < ref[:, 3].mean() / 3, (its, ref[:, 3])
+
+
+def test_stepper_switches_pressure_solvers(sem):
+    """Jacobi-PCG (graph replay), then GMRES + HSMG (direct launches, FP64 V-cycle),
+    then Jacobi-PCG again, 5 steps each with tight tolerances: the history follows
+    the oracle stepper throughout; bad arguments are rejected."""
+    torch, dev = torch_dev()
+    N, nel, nu, dt = 5, (4, 4, 4), 1.0 / 1600, 2e-3
+    ctx, m, v = pair(sem, N, nel, 0.0)
+    T = sem.TGV(ctx, nu, dt, vel=sem.opts(tol=1e-12, abs_tol=False), pres=sem.opts(tol=1e-10, abs_tol=False))
+    x, y, z = gpu_coords(ctx)
+    u, vv, w, p = inputs.tgv_initial(x, y, z, lib=torch)
+    T.set(u.contiguous(), vv.contiguous(), (w + 0 * x).contiguous(), p.contiguous())
+    stream = torch.cuda.Stream()
+    d = []
+    with torch.cuda.stream(stream):
+        d += T.step(5, stream=stream)
+        T.set_pressure_solver("gmres_hsmg", restart=20, vcycle="f64")
+        d += T.step(5, stream=stream)
+        T.set_pressure_solver("pcg")
+        d += T.step(5, stream=stream)
+    for bad in (dict(restart=0), dict(restart=65), dict(vcycle="bf16_tc")):
+        with pytest.raises(sem.SemError):
+            T.set_pressure_solver("gmres_hsmg", **bad)
+    T.close()
+    assert all(r["status"] == 0 for r in d), d
+    O = oracle.TGV(N, nel, v, (TWO_PI,) * 3, nu, dt, tol_v=1e-12, tol_p=1e-10, abs_tol=False)
+    O.set(*inputs.tgv_initial(*m.xyz))
+    ref = O.step(15)
+    assert rel([r["ke"] for r in d], ref[:, 1]) <= 1e-9
+    assert rel([r["enstrophy"] for r in d], ref[:, 2]) <= 1e-8
+    its = [r["iters"][0] for r in d]
+    assert max(its[5:10]) < min(its[10:]), its   # GMRES + HSMG against Jacobi-PCG iterations
