@@ -1117,8 +1117,12 @@ int orc_tgv_step(void *hnd, int nsteps, double *diag)
                          s->B[p] * ((b[0] * s->u[0][c][p] + b[1] * s->u[1][c][p] + b[2] * s->u[2][c][p]) / dt -
                                     gr[c * nL + p]);
             orc_dssum(N, s->nelx, s->nely, s->nelz, s->periodic, rhs);
-            /* new velocity goes into the oldest level, which is shifted out */
-            memcpy(s->u[2][c], s->u[0][c], sizeof(double) * nL);
+            /* new velocity goes into the oldest level, which is shifted out; the
+             * solve starts from the extrapolated velocity sum_j a_j u^{n+1-j}
+             * (the EXT weights of this step; this build's reading: the paper does
+             * not state the initial guess) */
+            for (size_t p = 0; p < nL; ++p)
+                s->u[2][c][p] = a[0] * s->u[0][c][p] + a[1] * s->u[1][c][p] + a[2] * s->u[2][c][p];
             rc = orc_pcg(N, s->nelx, s->nely, s->nelz, s->periodic, s->D, s->G, s->B, s->nu, b0 / dt,
                          rhs, s->u[2][c], s->tol_v, s->abs_tol, s->maxit, info);
             itu[c] = (int)info[0];

@@ -414,6 +414,24 @@ struct FArgs {
     int s32;
 };
 
+// Initial guess of the velocity solves: u_c^* = sum_j a_j u_c^{n+1-j} (the EXT
+// weights of the step), from the stored histories into the FP64 iterate.
+struct XArgs {
+    const void *u[3][3];  // [level][comp], stored fields
+    double *x[3];
+    int s32;
+};
+
+__global__ void k_tgv_ext(XArgs a, Coef k, int64_t nL)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nL) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        a.x[c][q] = k.a[0] * ld_fs(a.u[0][c], q, a.s32) + k.a[1] * ld_fs(a.u[1][c], q, a.s32) +
+                    k.a[2] * ld_fs(a.u[2][c], q, a.s32);
+}
+
 __global__ void k_tgv_F(FArgs a, Coef k, int64_t nL)
 {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1006,13 +1024,16 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     for (int cc = 0; cc < 3; ++cc) {
         rc = sem_dssum_dev(c, T->rhs[cc], SEM_F64, s);
         if (rc) return rc;
-        if (s32) {
-            k_conv_f32_f64<<<conv_grid(nL), 256, 0, s>>>(T->u32[0][cc], T->unew[cc], nL);
-            SEM_CHECK_LAUNCH();
-        } else {
-            SEM_CUDA(cudaMemcpyAsync(T->unew[cc], T->u[0][cc], bytes, cudaMemcpyDeviceToDevice, s));
-        }
     }
+    // the solves start from the extrapolated velocity (EXT weights of the step)
+    XArgs xa;
+    for (int cc = 0; cc < 3; ++cc) {
+        xa.x[cc] = T->unew[cc];
+        for (int l = 0; l < 3; ++l) xa.u[l][cc] = fu(T, l, cc);
+    }
+    xa.s32 = s32;
+    k_tgv_ext<<<(unsigned)sem_ceil_div(nL, 256), 256, 0, s>>>(xa, k, nL);
+    SEM_CHECK_LAUNCH();
     const double *bb[3] = {T->rhs[0], T->rhs[1], T->rhs[2]};
     double *xx[3] = {T->unew[0], T->unew[1], T->unew[2]};
     // (workspace slots 5-7; slot 4 keeps the pressure's Jacobi inverse between steps)
