@@ -323,6 +323,9 @@ typedef struct sem_hsmg sem_hsmg;
  * (smoother, transfers, level operators).  Creates one context per coarser
  * level (sem_setup on the same vertices) and allocates about 3 E-vectors per
  * level plus the factor tables; the caller's ctx must outlive the object.
+ * The coarse solve runs on workspace slot 0 of the coarsest level's context,
+ * which is the caller's ctx when nlev = 1 (the slot sem_pcg_solve uses).  One
+ * call at a time per object (its vectors are shared by its calls).
  * SEM_ERR_ARG: bad orders, N > 9, dtype, h1 <= 0, h2 < 0, coarse_tol <= 0 or
  * coarse_maxit < 1; SEM_ERR_NOMEM. */
 SEM_API int sem_hsmg_create(sem_ctx *ctx, int nlev, const int *orders, double h1, double h2,
