@@ -1027,7 +1027,7 @@ int orc_tgv_get(void *hnd, double *u0, double *u1, double *u2, double *p)
  *     (Dt_c^T g)_i = sum_q B_q (d phi_i/dx_c)(q) g(q); PCG from p^n,
  *     h1 = 1, h2 = 0 (singular: mean removal)
  *  5. (nu A + (b0/dt) B) u^{n+1}_c = dssum( F_c + B sum_j (b_j/dt) u^{n+1-j}_c
- *                                           - B dp/dx_c ),  PCG from u^n_c,
+ *                                           - B dp/dx_c ),  PCG from sum_j a_j u^{n+1-j}_c,
  *  6. shift histories; diagnostics KE, enstrophy at t^{n+1}.
  * diag[s*10 + ...] = {t, KE, enstrophy, it_p, it_u, it_v, it_w, status, dt of the
  * step, CFL of the new velocity for that dt}. */

@@ -1005,7 +1005,7 @@ static int step_once(sem_tgv *T, int q, cudaStream_t s)
     else
         k_tgv_log_iters<<<1, 32, 0, s>>>(st0, stride, io, so, serr, 0, 1, T->dev, T->log, 1);
     SEM_CHECK_LAUNCH();
-    // 5. velocity right-hand sides and the three Helmholtz solves from u^n
+    // 5. velocity right-hand sides and the three Helmholtz solves (from the extrapolated velocity)
     VArgs va;
     for (int cc = 0; cc < 3; ++cc) {
         va.F[cc] = T->F[cc];
