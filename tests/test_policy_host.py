@@ -141,11 +141,17 @@ def _fake_tgv_class(histories, speed=None):
     set_dt(cfl_target=...) its steps follow the CFL rule for a CFL number of
     speed[config] * dt."""
     class FakeTGV:
+        pressure_kinds = []
+
         def __init__(self, ctx, nu, dt, op, vel, pres):
             self.dt, self.n, self.cfg, self.t, self.target, self.dt_max = dt, 0, None, 0.0, 0.0, 0.0
 
         def set_dt(self, dt=0.0, cfl_target=0.0, dt_max=0.0):
             self.target, self.dt_max = cfl_target, dt_max
+
+        def set_pressure_solver(self, kind="gmres_hsmg", restart=30, vcycle="f32"):
+            assert kind in ("pcg", "gmres_hsmg")
+            FakeTGV.pressure_kinds.append(kind)
 
         def set_policy(self, rules):
             self.cfg = [k for k, v in policy.TABLE2.items() if all(rules[0][b] == v[b] for b in v)][0]
@@ -324,3 +330,23 @@ def test_peak_on_uneven_samples():
     t = [0.0, 0.3, 0.5, 1.1, 1.2]
     tp, yp = policy.peak(t, [2 - 3 * (x - 0.61) ** 2 for x in t])
     assert tp == pytest.approx(0.61, abs=1e-12) and yp == pytest.approx(2.0, abs=1e-12)
+
+
+def test_pressure_solver_option_reaches_the_stepper(monkeypatch):
+    """replay() and long_run() with pressure="gmres_hsmg" switch every run's stepper to
+    the GMRES + HSMG pressure solve (and leave it alone for "pcg"); the rows say which."""
+    import math
+
+    def a0(t):
+        return 0.125 * math.exp(-t), 0.375 * (1 + t), 0
+
+    _patch_gpu(monkeypatch, {"A-0": a0, "A-1": a0})
+    from paper_2608_24348_gb300 import sem as sem_mod
+    kinds = sem_mod.TGV.pressure_kinds
+    policy.replay(["A-1"], nel=2, N=3, dt=0.01, steps=8, warm=3, pressure="gmres_hsmg")
+    assert kinds == ["gmres_hsmg", "gmres_hsmg"]
+    rows = policy.long_run(["A-0"], nel=2, N=3, re=2.0, dt=0.01, t_end=0.1, projection=0, chunk=5,
+                           pressure="gmres_hsmg")
+    assert kinds == ["gmres_hsmg"] * 3 and rows[0]["pressure"] == "gmres_hsmg"
+    policy.long_run(["A-0"], nel=2, N=3, re=2.0, dt=0.01, t_end=0.1, projection=0, chunk=5)
+    assert len(kinds) == 3
